@@ -1,0 +1,195 @@
+"""Seeded synthetic survey inputs shared by the tests, the smoke check and the benchmark.
+
+This module only draws inputs: exposure epochs and pointings, observer
+positions, noise images, candidate-orbit states and the states and fluxes of
+injected sources.  It never propagates a candidate orbit, never projects a
+position into pixels and never evaluates the matched filter: sources are
+rendered at pixel positions that the caller supplies (computed by whichever
+implementation is under test, or by the oracle in the tests).
+
+The telescope pointing of each exposure follows a crude survey schedule: the
+field centre tracks a reference body on a circular orbit in the ecliptic,
+seen from the observer without light-time.  That is how a survey picks where
+to look, not part of the method, and nothing checks its accuracy.
+
+Units: AU, days, degrees for the WCS.  Frame: heliocentric ecliptic.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GAUSS_K = 0.01720209895                 # AU^1.5 / day (sampling of circular speeds)
+KMS_TO_AUD = 86400.0 / 149597870.7      # km/s -> AU/day
+OBLIQUITY_DEG = 84381.406 / 3600.0      # for turning a pointing into RA/Dec
+
+
+@dataclasses.dataclass
+class Exposures:
+    mjd: np.ndarray      # (n,)     epoch, days
+    obs: np.ndarray      # (n, 3)   observer position, AU
+    crval: np.ndarray    # (n, 2)   tangent point RA, Dec, deg
+    crpix: np.ndarray    # (n, 2)   0-based pixel of the tangent point
+    cd: np.ndarray       # (n, 2, 2) deg / px
+    sigma: np.ndarray    # (n,)     PSF sigma, px
+    var: np.ndarray      # (n,)     constant per-pixel variance
+    width: np.ndarray    # (n,) int32
+    height: np.ndarray   # (n,) int32
+
+    @property
+    def n(self) -> int:
+        return len(self.mjd)
+
+    def subset(self, idx) -> "Exposures":
+        idx = np.asarray(idx)
+        return Exposures(*[np.asarray(getattr(self, f.name))[idx] for f in dataclasses.fields(self)])
+
+
+@dataclasses.dataclass
+class Sky:
+    """A synthetic survey: exposures, candidate orbits and injected sources."""
+    name: str
+    ex: Exposures
+    t0: float                     # epoch of every orbit state
+    states: np.ndarray            # (n_o, 6) candidate orbits x, y, z, vx, vy, vz
+    inj_states: np.ndarray        # (n_inj, 6) injected sources
+    inj_flux: np.ndarray          # (n_inj,) flux (counts) of each injected source
+    inj_orbit: np.ndarray         # (n_inj,) candidate index equal to each injected source, or -1
+    seed: int
+    families: tuple | None = None  # (fam_orb_off int64, fam_exp_off int64, fam_exp_idx int32)
+    meta: dict = dataclasses.field(default_factory=dict)
+
+
+def observer_position(t, t_ref, theta_ref):
+    """Massless observer on a circular 1 AU orbit in the ecliptic (angular rate k rad/day)."""
+    th = theta_ref + GAUSS_K * (np.asarray(t, dtype=np.float64) - t_ref)
+    return np.stack([np.cos(th), np.sin(th), np.zeros_like(th)], axis=-1)
+
+
+def ecliptic_to_radec_deg(vec):
+    """Direction of an ecliptic vector as (RA, Dec) in degrees (pointing only)."""
+    e = math.radians(OBLIQUITY_DEG)
+    x, y, z = vec[..., 0], vec[..., 1], vec[..., 2]
+    qy = math.cos(e) * y - math.sin(e) * z
+    qz = math.sin(e) * y + math.cos(e) * z
+    ra = np.degrees(np.arctan2(qy, x)) % 360.0
+    dec = np.degrees(np.arctan2(qz, np.hypot(x, qy)))
+    return np.stack([ra, dec], axis=-1)
+
+
+def circular_reference(t, t_ref, r, lon_ref):
+    """Reference body for pointings: circular ecliptic orbit of radius r."""
+    th = lon_ref + GAUSS_K / r ** 1.5 * (np.asarray(t, dtype=np.float64) - t_ref)
+    return np.stack([r * np.cos(th), r * np.sin(th), np.zeros_like(th)], axis=-1)
+
+
+def tracking_pointings(mjd, obs, t_ref, r_ref, lon_ref):
+    """Field centres that follow a circular reference body (no light-time)."""
+    ref = circular_reference(mjd, t_ref, r_ref, lon_ref)
+    return ecliptic_to_radec_deg(ref - obs)
+
+
+def grid_states(r_values, dv_r_kms, dv_t_kms, lon):
+    """Orbit grid of the tiny workloads: every node starts on the heliocentric
+    ray at longitude ``lon`` (in the ecliptic) at distance r, with the circular
+    prograde speed plus (dv_r, dv_t) km/s along the radial and tangential unit
+    vectors.  Index o = (i_r * n_vr + i_vr) * n_vt + i_vt."""
+    rh = np.array([math.cos(lon), math.sin(lon), 0.0])
+    th = np.array([-math.sin(lon), math.cos(lon), 0.0])
+    R, VR, VT = np.meshgrid(np.asarray(r_values, dtype=np.float64),
+                            np.asarray(dv_r_kms, dtype=np.float64) * KMS_TO_AUD,
+                            np.asarray(dv_t_kms, dtype=np.float64) * KMS_TO_AUD, indexing="ij")
+    R, VR, VT = R.ravel(), VR.ravel(), VT.ravel()
+    vc = GAUSS_K / np.sqrt(R)
+    pos = R[:, None] * rh[None, :]
+    vel = VR[:, None] * rh[None, :] + (vc + VT)[:, None] * th[None, :]
+    return np.concatenate([pos, vel], axis=1)
+
+
+def half_open_linspace(a, b, n):
+    return a + (b - a) * np.arange(n, dtype=np.float64) / n
+
+
+def flux_for_snr(snr, sigma_px, var):
+    """Flux giving a per-image matched-filter SNR of about ``snr`` (continuous
+    Gaussian approximation sum P^2 ~ 1 / (4 pi sigma^2))."""
+    return np.asarray(snr) * np.sqrt(var) * np.sqrt(4.0 * math.pi) * sigma_px
+
+
+def render_sources(images, xy, flux, sigma, radius=6.0):
+    """Add point sources to ``images`` (n_exp, H, W) in place.  ``xy`` is
+    (n_src, n_exp, 2) pixel coordinates (NaN = not visible), ``flux`` (n_src,),
+    ``sigma`` (n_exp,) PSF sigma.  Each source is a unit-integral sampled
+    Gaussian times its flux, drawn within ``radius`` sigma."""
+    n_exp, H, W = images.shape
+    for s in range(xy.shape[0]):
+        for j in range(n_exp):
+            x, y = xy[s, j]
+            if not (np.isfinite(x) and np.isfinite(y)):
+                continue
+            sg = float(sigma[j])
+            rad = int(math.ceil(radius * sg))
+            x0, x1 = max(int(math.floor(x)) - rad, 0), min(int(math.floor(x)) + rad + 2, W)
+            y0, y1 = max(int(math.floor(y)) - rad, 0), min(int(math.floor(y)) + rad + 2, H)
+            if x0 >= x1 or y0 >= y1:
+                continue
+            gx = np.exp(-0.5 * ((np.arange(x0, x1) - x) / sg) ** 2)
+            gy = np.exp(-0.5 * ((np.arange(y0, y1) - y) / sg) ** 2)
+            images[j, y0:y1, x0:x1] += (flux[s] / (2.0 * math.pi * sg * sg)
+                                        * np.outer(gy, gx)).astype(images.dtype)
+    return images
+
+
+# --------------------------------------------------------------------------
+# Tiny grid sky (the plain-method workload and its scaled-down test cases)
+# --------------------------------------------------------------------------
+
+def grid_sky(*, name="tiny", n_exp=10, nights=20.0, size=512, scale_arcsec=0.2,
+             n_r=16, n_v=64, r_range=(2.0, 3.0), v_kms=5.0, sigma_px=1.5, var=1.0,
+             inj_snr=2.0, n_inj=5, seed=1, mjd_start=60000.0, lon=0.7) -> Sky:
+    """Plain-method grid workload.  Epochs: one per ``nights / n_exp`` nights,
+    each jittered by U(-0.1, 0.1) d.  Observer on a circular 1 AU orbit, at
+    opposition to the grid's reference body at the epoch t0 (mid-span).
+    Pointings track the central node (r = 2.5 AU circular) along the ecliptic.
+    Orbit grid: n_r distances x n_v radial x n_v tangential velocity offsets
+    (half-open grids, so the circular central node is a grid point).
+    Injected sources: ``n_inj`` grid nodes at the central distance with zero
+    tangential offset and the smallest radial offsets; those stay in the
+    tracked field, so their on-sky tracks stay near the field centre."""
+    rng = np.random.default_rng(seed)
+    step = nights / n_exp
+    mjd = mjd_start + 0.5 + step * np.arange(n_exp) + rng.uniform(-0.1, 0.1, n_exp)
+    t0 = float(mjd_start + 0.5 + step * (n_exp - 1) / 2.0)
+    obs = observer_position(mjd, t0, lon)
+    r_c = 0.5 * (r_range[0] + r_range[1])
+    crval = tracking_pointings(mjd, obs, t0, r_c, lon)
+    s = scale_arcsec / 3600.0
+    ex = Exposures(
+        mjd=mjd, obs=obs, crval=crval,
+        crpix=np.tile(np.array([size / 2.0, size / 2.0]), (n_exp, 1)),
+        cd=np.tile(np.array([[-s, 0.0], [0.0, s]]), (n_exp, 1, 1)),
+        sigma=np.full(n_exp, sigma_px), var=np.full(n_exp, var),
+        width=np.full(n_exp, size, dtype=np.int32), height=np.full(n_exp, size, dtype=np.int32))
+    r_vals = half_open_linspace(r_range[0], r_range[1], n_r)
+    dv = half_open_linspace(-v_kms, v_kms, n_v)
+    states = grid_states(r_vals, dv, dv, lon)
+    i_r = int(np.argmin(np.abs(r_vals - r_c)))
+    i_t = int(np.argmin(np.abs(dv)))
+    order = np.argsort(np.abs(dv), kind="stable")[:n_inj]
+    inj_orbit = np.array([(i_r * n_v + i_v) * n_v + i_t for i_v in order], dtype=np.int64)
+    flux = flux_for_snr(np.full(n_inj, inj_snr), sigma_px, var)
+    return Sky(name=name, ex=ex, t0=t0, states=states, inj_states=states[inj_orbit].copy(),
+               inj_flux=flux, inj_orbit=inj_orbit, seed=seed,
+               meta=dict(r_values=r_vals, dv_kms=dv, size=size))
+
+
+def noise_images(ex: Exposures, seed: int, dtype=np.float32):
+    """N(0, var_j) noise, one image per exposure (numpy, seeded)."""
+    rng = np.random.default_rng(seed + 1000003)
+    out = np.empty((ex.n, int(ex.height[0]), int(ex.width[0])), dtype=dtype)
+    for j in range(ex.n):
+        out[j] = rng.standard_normal((int(ex.height[j]), int(ex.width[j])), dtype=np.float32) \
+            * np.float32(math.sqrt(ex.var[j]))
+    return out
