@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Throughput of the stacking hot path on one GB300 (or N independent replicas).
+
+One step = the whole hot path over one batch: matched-filter planes of every
+exposure (load_exposures), propagate/project/gather/stack of every orbit
+against every exposure (stack_orbits) and the top-k ranking
+(topk_candidates).  Workload: the MBA-scale synthetic survey (200 exposures
+of 4096 x 4096 over 30 nights, 1,000 injected main-belt asteroids, 16.4 M
+candidate orbits), inputs resident in HBM (26.8 GB of FP32 planes, far
+larger than L2).  ``value`` is orbit x exposure samples/s of the chosen form
+(BF16 planes, persistent work queue, CUDA graph, autotuned tiles); the plain
+form (FP32 planes, one thread per orbit) is measured in the same run.
+
+With ``--impl reference`` the same metric is measured for the FP64 CPU
+oracle on the host cores, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "orbit×exposure samples/s and vetted candidates/s at fixed recall, plain vs chosen"
+UNIT = "samples/s"
+# FP64 peak of one GB300 derived from unit counts and clock: 152 SMs x 2 FP64
+# FMA per SM per clock x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP64 flops executed per (orbit, exposure) sample by the stack kernel on this
+# workload, from ncu instruction counters (DFMA x 2 + DADD + DMUL) divided by
+# the samples of the captured launch; see the design doc (roofline section).
+FP64_FLOP_PER_SAMPLE = None
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--fam-size", type=int, default=16384, help="orbits per injected asteroid")
+    p.add_argument("--n-true", type=int, default=1000)
+    p.add_argument("--size", type=int, default=4096)
+    p.add_argument("--n-exp", type=int, default=200)
+    p.add_argument("--k", type=int, default=8192)
+    p.add_argument("--plane", default="bf16", choices=["f32", "bf16", "f16"])
+    p.add_argument("--forms", default="plain,chosen")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload ----
+
+def make_workload(args, rank, device):
+    import torch
+    from paper_2503_08854_gb300 import ndt, synth
+    sky = synth.mba_sky(n_exp=args.n_exp, size=args.size, n_true=args.n_true,
+                        fam_size=args.fam_size, seed=2 + rank)
+    stream = torch.cuda.Stream(device=device)
+    imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
+    # injected sources at positions from the library's own position kernel
+    ctx = ndt.create(device.index, stream)
+    try:
+        torch.cuda.synchronize(device)
+        ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype="f32")
+        st = torch.from_numpy(np.ascontiguousarray(sky.inj_states.T)).to(device)
+        xy = torch.empty(len(sky.inj_states) * sky.ex.n * 2, dtype=torch.float64, device=device)
+        torch.cuda.synchronize(device)
+        ndt.predict_positions(ctx, st, sky.t0, len(sky.inj_states), xy)
+    finally:
+        ndt.destroy(ctx)
+    synth.render_sources_torch(imgs, xy.view(len(sky.inj_states), sky.ex.n, 2), sky.inj_flux,
+                               sky.ex.sigma)
+    states = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(device)
+    torch.cuda.synchronize(device)
+    return sky, stream, imgs, states
+
+
+class Form:
+    def __init__(self, name, plane, mode, graph):
+        self.name, self.plane, self.mode, self.graph = name, plane, mode, graph
+
+
+def run_steps(ctx, stream, sky, imgs, states, k, n_steps, idx_out, snr_out, plane):
+    """Device-resident steps; per-step device time from CUDA events on the
+    library's stream, plus the stack kernel's own event time."""
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    n = states.shape[1]
+    step_ms, stack_ms = [], []
+    for _ in range(n_steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=plane)
+        ndt.stack_orbits(ctx, states, sky.t0, n)
+        ndt.topk_candidates(ctx, k, idx_out, snr_out)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stack_ms.append(ndt.get_stats(ctx)["last_stack_ms"])
+    return step_ms, stack_ms
+
+
+def recall_of(idx, sky):
+    fam = sky.meta["fam_size"]
+    hit = np.zeros(len(sky.inj_states), bool)
+    ok = idx >= 0
+    hit[np.unique(idx[ok] // fam)] = True
+    return float(hit.mean())
+
+
+def bench_form(args, form, sky, stream, imgs, states, device, barrier):
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    n = states.shape[1]
+    k = min(args.k, n)
+    ctx = ndt.create(device.index, stream)
+    try:
+        idx = torch.empty(k, dtype=torch.int64, device=device)
+        val = torch.empty(k, device=device)
+        tiles = None
+        if form.mode == "persistent":
+            ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=form.plane)
+            times = np.zeros(9, np.float32)
+            ndt.autotune(ctx, states, sky.t0, n, times_ms=times)
+            st = ndt.get_stats(ctx)
+            tiles = {"orbit_tile": st["orbit_tile"], "exp_tile": st["exp_tile"],
+                     "sweep_ms": [round(float(t), 2) for t in times]}
+            ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"],
+                           use_graph=form.graph)
+        run_steps(ctx, stream, sky, imgs, states, k, args.warmup, idx, val, form.plane)
+        launches0 = ndt.get_stats(ctx)["kernel_launches"]
+        barrier()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        step_ms, stack_ms = run_steps(ctx, stream, sky, imgs, states, k, args.steps, idx, val,
+                                      form.plane)
+        torch.cuda.synchronize(device)
+        wall = time.perf_counter() - t0
+        stats = ndt.get_stats(ctx)
+        launches = stats["kernel_launches"] - launches0
+        rec = recall_of(idx.cpu().numpy(), sky)
+        out = dict(step_ms=step_ms, stack_ms=stack_ms, wall_s=wall, launches=launches,
+                   valid=stats["valid_samples"], samples=stats["samples"], recall=rec,
+                   planes_ms=stats["last_planes_ms"], topk_ms=stats["last_topk_ms"], tiles=tiles,
+                   top_snr=float(val[0].item()))
+        e2e = None
+        if not args.no_e2e and form.name == "chosen":
+            e2e = bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device)
+        return out, e2e
+    finally:
+        ndt.destroy(ctx)
+
+
+def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
+    """Same steps through the public API with pinned HOST inputs and outputs:
+    the H2D copies of images and orbit states and the D2H read of the top-k
+    are inside the timed region."""
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    n = states.shape[1]
+    h_imgs = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
+    h_imgs.copy_(imgs)
+    h_states = torch.empty(states.shape, dtype=states.dtype, pin_memory=True)
+    h_states.copy_(states)
+    h_idx = torch.empty(k, dtype=torch.int64, pin_memory=True)
+    h_val = torch.empty(k, dtype=torch.float32, pin_memory=True)
+    np_imgs = h_imgs.numpy()
+    np_states = h_states.numpy()
+
+    def step():
+        ndt.load_exposures(ctx, sky.ex, np_imgs, plane_dtype=form.plane)
+        ndt.stack_orbits(ctx, np_states, sky.t0, n)
+        ndt.topk_candidates(ctx, k, h_idx.numpy(), h_val.numpy())
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    barrier()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize(device)
+    dt = (time.perf_counter() - t0) / args.steps
+    h2d = int(h_imgs.numel() * 4 + h_states.numel() * 8)
+    d2h = int(k * 12)
+    return dict(s_per_step=dt, h2d=h2d, d2h=d2h, recall=recall_of(h_idx.numpy(), sky))
+
+
+# ------------------------------------------------------------ cpu oracle ----
+
+def cpu_oracle_rate(sky, host_imgs, seconds, rng_seed=0):
+    """The FP64 oracle as it stands, on a bounded random sample of the orbits of
+    the same workload against all exposures, planes evaluated at the gathered
+    pixels from the same images.  Returns (samples/s, threads, description)."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    rng = np.random.default_rng(rng_seed)
+    n_exp = sky.ex.n
+    imgs = [host_imgs[j] for j in range(n_exp)]
+    m = 64
+    elapsed = 0.0
+    while True:
+        sel = np.sort(rng.choice(len(sky.states), m, replace=False))
+        t = time.perf_counter()
+        O.stack(sky.states[sel], sky.t0, sky.ex, images=imgs, nthreads=threads)
+        elapsed = time.perf_counter() - t
+        if elapsed >= 0.15 * seconds or m >= 2_000_000:
+            break
+        m = int(min(m * max(2.0, 0.3 * seconds / max(elapsed, 1e-3)), 2_000_000))
+    rate = m * n_exp / elapsed
+    return rate, threads, f"{m} random orbits x {n_exp} exposures ({m * n_exp} samples, {elapsed:.1f} s)"
+
+
+def reference_arm(args):
+    """--impl reference: the oracle, on the host cores, steps of a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2503_08854_gb300 import synth
+    sky = synth.mba_sky(n_exp=args.n_exp, size=args.size, n_true=args.n_true,
+                        fam_size=args.fam_size, seed=2)
+    imgs = synth.noise_images(sky.ex, sky.seed)   # numpy noise: the rate does not depend on values
+    threads = os.cpu_count() or 1
+    per_step = 2000
+    rng = np.random.default_rng(1)
+
+    def step():
+        sel = np.sort(rng.choice(len(sky.states), per_step, replace=False))
+        O.stack(sky.states[sel], sky.t0, sky.ex, images=list(imgs), nthreads=threads)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = (time.perf_counter() - t) / args.steps
+    v = per_step * sky.ex.n / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"MBA-scale survey: {sky.ex.n} exposures {args.size}^2, "
+                                   f"{len(sky.states)} candidate orbits (sampled)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} random orbits x {sky.ex.n} exposures per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------- main ----
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    from paper_2503_08854_gb300 import __name__ as _pkg  # noqa: F401
+    import __graft_entry__
+    __graft_entry__.build()
+    sky, stream, imgs, states = make_workload(args, rank, device)
+    forms = {"plain": Form("plain", "f32", "plain", False),
+             "chosen": Form("chosen", args.plane, "persistent", True)}
+    results, e2e = {}, None
+    clocks = ClockSampler(local)
+    clocks.start()
+    for name in args.forms.split(","):
+        res, e = bench_form(args, forms[name], sky, stream, imgs, states, device, barrier)
+        results[name] = res
+        if e is not None:
+            e2e = e
+    clk = clocks.stop()
+    head = "chosen" if "chosen" in results else list(results)[0]
+    r = results[head]
+    samples = r["samples"]
+    step_s = max_over_ranks(statistics.mean(r["step_ms"]) / 1e3)
+    value = samples * world / step_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"MBA-scale survey: {sky.ex.n} exposures {args.size}x{args.size}, "
+                               f"{states.shape[1]} candidate orbits ({args.n_true} families), "
+                               f"all orbits x all exposures, top-{min(args.k, states.shape[1])}",
+                   "form": head, "planes": forms[head].plane,
+                   "launch": forms[head].mode + ("+graph" if forms[head].graph else ""),
+                   "tiles": r["tiles"], "l2": "inputs larger than L2 (planes >= 13 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "valid_samples_per_s": r["valid"] * world / step_s,
+        "candidates_per_s": min(args.k, states.shape[1]) * world / step_s,
+        "recall": r["recall"],
+        "gpu_launches": int(r["launches"]),
+        "clocks": clk,
+    }
+    for name, res in results.items():
+        s = statistics.mean(res["step_ms"]) / 1e3
+        line[name] = {"samples_per_s": res["samples"] / s, "ms_per_step": s * 1e3,
+                      "stack_ms": statistics.mean(res["stack_ms"]), "planes_ms": res["planes_ms"],
+                      "topk_ms": res["topk_ms"], "recall": res["recall"],
+                      "valid_fraction": res["valid"] / max(res["samples"], 1)}
+    stack_s = statistics.mean(r["stack_ms"]) / 1e3
+    if FP64_FLOP_PER_SAMPLE is not None:
+        ach = FP64_FLOP_PER_SAMPLE * samples / stack_s / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                            "kernel": "k_stack_persistent (FP64 pipe)"}
+    else:
+        line["roofline"] = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
+                            "unit": "TFLOP/s", "frac": None, "traffic": None,
+                            "note": "FP64 flop/sample not yet measured", "stack_samples_per_s":
+                            samples / stack_s}
+    if e2e is not None:
+        line["e2e"] = {"value": samples * world / max_over_ranks(e2e["s_per_step"]), "unit": UNIT,
+                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                       "recall": e2e["recall"]}
+    if rank == 0 and not args.no_cpu:
+        host = imgs.cpu().numpy()
+        rate, cores, desc = cpu_oracle_rate(sky, host, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * ndt.h -- C ABI of the GB300 non-linear digital tracking library
+ * (after Golovich et al., "Survey-Wide Asteroid Discovery with a
+ * High-Performance Computing Enabled Non-Linear Digital Tracking
+ * Framework", arXiv 2503.08854).
+ *
+ * The library runs the data-parallel hot path of the paper's Algorithm 1 on
+ * one GPU: for every candidate orbit it propagates the orbit to each
+ * exposure epoch (two-body motion about the Sun, sec. 3), applies light time
+ * and the observer position, projects through the exposure's tangent-plane
+ * WCS (sec. 3), gathers matched-filter planes psi, phi at the nearest pixel
+ * (sec. 3, Gaussian-PSF matched filter) and accumulates the constant-flux
+ * stacked statistic (sec. 3, "same flux in each image"), then ranks orbits
+ * (Algorithm 1, FindSignificantResults).
+ *
+ * Conventions shared by every entry point
+ *   Units        AU, days (one uniform time scale), degrees in the WCS.
+ *   Frame        heliocentric ecliptic, Sun fixed at the origin.
+ *   Orbits       Cartesian state at a common epoch t0, structure of arrays:
+ *                states[c * n_orbits + o], c = 0..5 -> x, y, z, vx, vy, vz
+ *                (AU, AU/day), FP64.
+ *   Pointers     every array argument may be host memory (pageable or
+ *                pinned) or device memory of the context's device; the
+ *                library detects which and copies host data through
+ *                context-owned device buffers.  The caller owns every
+ *                argument buffer; the context owns planes, metadata and
+ *                scratch.
+ *   Streams      work is issued on the stream given to ndt_create; entry
+ *                points that return results in host memory synchronise it.
+ *   Errors       every call returns an ndt_status; ndt_last_error() gives a
+ *                one-line description.  No entry point aborts the process.
+ *                A device-side failure (a Kepler solve that did not converge)
+ *                is counted on the device and reported as NDT_ENOCONV by the
+ *                call that reads results back.
+ *   Threads      a context is not thread safe; use one per host thread.
+ */
+#ifndef NDT_H
+#define NDT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NDT_OK = 0,
+  NDT_EINVAL = 1,   /* bad argument (null pointer, size, layout)          */
+  NDT_ENOMEM = 2,   /* device or host allocation failed                     */
+  NDT_ECUDA = 3,    /* CUDA runtime error (message in ndt_last_error)       */
+  NDT_ETIMEOUT = 4, /* a bounded device wait gave up                        */
+  NDT_ESTATE = 5,   /* call out of order (e.g. stack before load)           */
+  NDT_ENOCONV = 6   /* some Kepler solves did not converge                  */
+} ndt_status;
+
+typedef enum {
+  NDT_PLANE_F32 = 0,  /* psi, phi stored as FP32                             */
+  NDT_PLANE_BF16 = 1, /* BF16 values times a per-exposure FP32 scale         */
+  NDT_PLANE_F16 = 2   /* FP16 values times a per-exposure FP32 scale         */
+} ndt_plane_dtype;
+
+typedef enum {
+  NDT_LAUNCH_PLAIN = 0,      /* one thread per orbit over all its exposures  */
+  NDT_LAUNCH_PERSISTENT = 1  /* persistent work queue of (family, orbit tile,
+                                exposure tile) items                        */
+} ndt_launch_mode;
+
+/* One exposure (paper sec. 3: image header with epoch, WCS and PSF width,
+   observer location at the time of the image).  112 bytes, no padding. */
+typedef struct {
+  double mjd;          /* epoch, days                                      */
+  double obs_xyz[3];   /* observer position, heliocentric ecliptic, AU     */
+  double crval[2];     /* tangent point RA, Dec (equatorial), degrees      */
+  double crpix[2];     /* tangent point pixel, 0-based (FITS CRPIX - 1)    */
+  double cd[4];        /* CD matrix row-major: [CD1_1 CD1_2 CD2_1 CD2_2],
+                          degrees per pixel                                */
+  float psf_sigma_px;  /* Gaussian PSF sigma, pixels, in (0, 4]            */
+  float variance;      /* constant per-pixel noise variance (> 0), used
+                          when no variance plane is given                  */
+  int32_t width;       /* pixels, 1 .. 32768                               */
+  int32_t height;      /* pixels, 1 .. 32768                               */
+} ndt_exposure;
+
+/* Counters of one context, for benchmarking and tests. */
+typedef struct {
+  int64_t kernel_launches;   /* kernels this context has launched           */
+  int64_t samples;           /* (orbit, exposure) pairs of the last stack   */
+  int64_t valid_samples;     /* of which in bounds                          */
+  int64_t kepler_failures;   /* solves that hit the iteration limit         */
+  float last_stack_ms;       /* device time of the last stack kernel        */
+  float last_planes_ms;      /* device time of the last plane computation   */
+  float last_topk_ms;        /* device time of the last top-k               */
+  int32_t orbit_tile;        /* persistent-launch tile shape in use         */
+  int32_t exp_tile;
+  int32_t launch_mode;
+  int32_t plane_dtype;
+} ndt_stats;
+
+typedef struct ndt_ctx ndt_ctx;
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+   (a cudaStream_t; NULL = the legacy default stream).  *out is set to NULL
+   on failure. */
+ndt_status ndt_create(ndt_ctx **out, int device, void *cuda_stream);
+
+/* Free every device buffer of the context.  NULL is accepted. */
+void ndt_destroy(ndt_ctx *ctx);
+
+/* Description of the last error of this context (never NULL).  With a NULL
+   context it describes the last failed ndt_create. */
+const char *ndt_last_error(const ndt_ctx *ctx);
+
+/* Physical constants used by propagation and light time.  Defaults: GM_sun
+   = k^2 with the Gaussian constant k = 0.01720209895 AU^1.5/day, c =
+   173.1446326742403 AU/day, obliquity 84381.406 arcsec.  gm <= 0 selects
+   force-free (straight-line) motion, c <= 0 disables light time. */
+ndt_status ndt_set_constants(ndt_ctx *ctx, double gm, double c_light, double obliquity_rad);
+
+/*
+ * load_exposures: store the exposure table and compute the matched-filter
+ * planes of every image (paper sec. 3: matched filter with a Gaussian PSF
+ * whose width is given in the image header):
+ *   psi_j(p) = sum_k P_j(k) I_j(p+k) / V_j(p+k),
+ *   phi_j(p) = sum_k P_j(k)^2 / V_j(p+k),
+ * P_j the Gaussian of sigma_j truncated at R = ceil(4 sigma_j) and
+ * normalised to unit sum over its (2R+1)^2 window; terms outside the image
+ * are dropped.  `images[j]` is a row-major FP32 height x width image;
+ * `variances` is NULL (constant variance from the table) or n_exp per-pixel
+ * FP32 variance planes of the same shape.  `plane_dtype` is an
+ * ndt_plane_dtype.  Replaces any previous exposure set.  Returns NDT_EINVAL
+ * for n_exp < 1, a null image, sigma outside (0, 4], variance <= 0, a
+ * singular CD matrix or a non-finite epoch.
+ */
+ndt_status ndt_load_exposures(ndt_ctx *ctx, const ndt_exposure *meta, int32_t n_exp,
+                              const float *const *images, const float *const *variances,
+                              int32_t plane_dtype);
+
+/*
+ * stack_orbits: for every orbit o and every exposure j of its family,
+ * propagate o to the epoch of j (two-body, paper sec. 3), correct for light
+ * time, project through the WCS of j, and if the nearest pixel
+ * (floor(x + 1/2), floor(y + 1/2)) lies inside the image add psi_j, phi_j
+ * there to the orbit's sums (paper sec. 3, filter to image boundaries and
+ * combine assuming constant flux):
+ *   Psi_o = sum psi,  Phi_o = sum phi,  n_o = number of valid samples,
+ *   nu_o  = Psi_o / sqrt(Phi_o) if Phi_o > 0 and n_o >= min_obs, else -inf.
+ * Families (CSR): family f owns orbits [fam_orbit_off[f], fam_orbit_off[f+1])
+ * and tests exposures fam_exp_idx[fam_exp_off[f] .. fam_exp_off[f+1]);
+ * n_fam = 0 (and null CSR arrays) means every orbit tests every exposure.
+ * fam_orbit_off must start at 0, end at n_orbits and be non-decreasing;
+ * exposure indices must be in [0, n_exp) and unique within a family.
+ * Outputs (each n_orbits long; any may be NULL): psi_sum, phi_sum (FP32),
+ * nobs (int32), snr (FP32).  The per-orbit nu always stays in the context
+ * for ndt_topk_candidates.  Sums are accumulated in FP32 with compensation;
+ * geometry is FP64.
+ */
+ndt_status ndt_stack_orbits(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
+                            const int64_t *fam_orbit_off, const int64_t *fam_exp_off,
+                            const int32_t *fam_exp_idx, int32_t n_fam, int32_t min_obs,
+                            float *psi_sum, float *phi_sum, int32_t *nobs, float *snr);
+
+/*
+ * topk_candidates: the k orbits of the last stack with the largest nu,
+ * sorted by nu descending and orbit index ascending (paper Algorithm 1,
+ * FindSignificantResults).  k is clamped to the number of orbits; the
+ * number written is returned in *k_out (may be NULL).  idx_out (int64) and
+ * snr_out (FP32) hold k entries each; either may be NULL.
+ */
+ndt_status ndt_topk_candidates(ndt_ctx *ctx, int64_t k, int64_t *idx_out, float *snr_out,
+                               int64_t *k_out);
+
+/*
+ * predict_positions: pixel coordinates of every orbit in every loaded
+ * exposure, computed by the same device code as stack_orbits:
+ * xy_out[(o * n_exp + j) * 2 + {0, 1}] = (x, y), or NaN when the exposure's
+ * tangent point is 90 degrees or more away (cos c <= 0).  j follows the
+ * order of the table given to load_exposures.  FP64, n_orbits * n_exp * 2.
+ */
+ndt_status ndt_predict_positions(ndt_ctx *ctx, const double *states, double t0,
+                                 int64_t n_orbits, double *xy_out);
+
+/* Decode the stored planes of exposure j (table order) into row-major FP32
+   psi_out, phi_out (height x width each; either may be NULL). */
+ndt_status ndt_get_planes(ndt_ctx *ctx, int32_t j, float *psi_out, float *phi_out);
+
+/* Select the launch form of stack_orbits: NDT_LAUNCH_PLAIN, or
+   NDT_LAUNCH_PERSISTENT with orbit_tile in {32, 64, 128} and exp_tile in
+   {8, 16, 32}; use_graph != 0 replays the persistent stack through a
+   captured CUDA graph when the arguments repeat. */
+ndt_status ndt_set_launch(ndt_ctx *ctx, int32_t mode, int32_t orbit_tile, int32_t exp_tile,
+                          int32_t use_graph);
+
+/*
+ * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}
+ * and exp_tile in {8, 16, 32} on the given workload (arguments as for
+ * ndt_stack_orbits, without outputs), keep the fastest shape for the
+ * context and write the 9 timings (ms, row-major [orbit_tile][exp_tile]) to
+ * times_ms (may be NULL).
+ */
+ndt_status ndt_autotune(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
+                        const int64_t *fam_orbit_off, const int64_t *fam_exp_off,
+                        const int32_t *fam_exp_idx, int32_t n_fam, float *times_ms);
+
+/* Copy the context's counters into *out. */
+ndt_status ndt_get_stats(ndt_ctx *ctx, ndt_stats *out);
+
+/* Wait for all work issued by the context. */
+ndt_status ndt_synchronize(ndt_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NDT_H */

@@ -1,0 +1,759 @@
+// api.cu -- the C ABI of include/ndt.h: context, device memory, host/device
+// argument handling, exposure tables and launch sequencing.  All numerical
+// work runs in the kernels of k_planes.cu, k_stack.cu and k_topk.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "ndt.h"
+#include "ndt_internal.cuh"
+
+using namespace ndt;
+
+namespace {
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(bytes, 256);
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) { p = nullptr; return e; }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+char g_create_error[256] = "no error";
+
+constexpr double kPi = 3.14159265358979323846;
+
+}  // namespace
+
+struct ndt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_sms = 0;
+  std::string err = "no error";
+  Phys ph{};
+  double obliquity = 0.0;
+  // exposures (sorted by epoch on the device)
+  int32_t n_exp = 0;
+  std::vector<ndt_exposure> table;
+  std::vector<int32_t> sorted_to_table, table_to_sorted;
+  std::vector<ExpDev> ex_host;
+  int plane_type = kF32;
+  DevBuf ex_dev, pos_to_table_dev, planes, planes_tmp, jobs_dev, absmax_dev, scales_dev;
+  DevBuf stage_images, stage_vars;
+  // orbit batch
+  DevBuf stage_states, snr, out_tmp, xy_tmp;
+  int64_t last_n = 0;
+  // families and queue
+  DevBuf fam_orb_off, fam_exp_off, fam_exp_pos, item_off, fam_order;
+  DevBuf queue_head, counters;
+  // top-k
+  DevBuf topk_scratch, topk_out;
+  // launch form
+  int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned char> graph_key;
+  // stats
+  int64_t launches = 0, samples = 0;
+  cudaEvent_t ev[6] = {};
+  bool have_stack_ev = false, have_planes_ev = false, have_topk_ev = false;
+};
+
+namespace {
+
+ndt_status fail(ndt_ctx* c, ndt_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c->err = buf;
+  return s;
+}
+
+ndt_status cuda_fail(ndt_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? NDT_ENOMEM : NDT_ECUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define NDT_CK(call, what)                                  \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Make `src` (host or device, `bytes` long) available on the device.
+ndt_status to_device(ndt_ctx* ctx, const void* src, size_t bytes, DevBuf& stage, const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return NDT_OK;
+  }
+  NDT_CK(stage.ensure(bytes), "staging allocation");
+  NDT_CK(cudaMemcpyAsync(stage.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream), "H2D copy");
+  *out = stage.p;
+  return NDT_OK;
+}
+
+void set_default_phys(ndt_ctx* c, double gm, double cl, double eps) {
+  c->ph.gm = gm;
+  c->ph.force_free = gm > 0.0 ? 0 : 1;
+  c->ph.sqrt_gm = gm > 0.0 ? std::sqrt(gm) : 1.0;
+  c->ph.inv_gm = gm > 0.0 ? 1.0 / gm : 0.0;
+  c->ph.inv_c = cl > 0.0 ? (float)(1.0 / cl) : 0.0f;
+  c->obliquity = eps;
+}
+
+// Tangent-plane rows of one exposure in the ecliptic frame (TAN projection,
+// Calabretta & Greisen 2002, sec. 5.1.3, with the inverse CD matrix folded in).
+void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
+  const double d2r = kPi / 180.0;
+  const double a0 = m.crval[0] * d2r, d0 = m.crval[1] * d2r;
+  const double ca = std::cos(a0), sa = std::sin(a0), cdl = std::cos(d0), sdl = std::sin(d0);
+  const double p0[3] = {cdl * ca, cdl * sa, sdl};
+  const double ea[3] = {-sa, ca, 0.0};
+  const double no[3] = {-sdl * ca, -sdl * sa, cdl};
+  const double det = m.cd[0] * m.cd[3] - m.cd[1] * m.cd[2];
+  const double i00 = m.cd[3] / det, i01 = -m.cd[1] / det, i10 = -m.cd[2] / det, i11 = m.cd[0] / det;
+  const double r2d = 180.0 / kPi;
+  double ax[3], ay[3];
+  for (int i = 0; i < 3; ++i) {
+    ax[i] = r2d * (i00 * ea[i] + i01 * no[i]);
+    ay[i] = r2d * (i10 * ea[i] + i11 * no[i]);
+  }
+  // rows act on equatorial vectors q = R_x(eps) rho; fold R_x(eps)^T in
+  const double ce = std::cos(eps), se = std::sin(eps);
+  auto to_ecl = [&](const double w[3], double out[3]) {
+    out[0] = w[0];
+    out[1] = ce * w[1] + se * w[2];
+    out[2] = -se * w[1] + ce * w[2];
+  };
+  to_ecl(p0, e.p0);
+  to_ecl(ax, e.ax);
+  to_ecl(ay, e.ay);
+  e.crpix[0] = m.crpix[0];
+  e.crpix[1] = m.crpix[1];
+}
+
+void record(ndt_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
+
+}  // namespace
+
+extern "C" {
+
+ndt_status ndt_create(ndt_ctx** out, int device, void* cuda_stream) {
+  if (!out) return NDT_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || device < 0 || device >= ndev) {
+    snprintf(g_create_error, sizeof g_create_error, "no CUDA device %d (%s)", device,
+             e == cudaSuccess ? "out of range" : cudaGetErrorString(e));
+    return e == cudaSuccess ? NDT_EINVAL : NDT_ECUDA;
+  }
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    snprintf(g_create_error, sizeof g_create_error, "cudaSetDevice: %s", cudaGetErrorString(e));
+    return NDT_ECUDA;
+  }
+  ndt_ctx* c = new ndt_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device);
+  set_default_phys(c, 0.01720209895 * 0.01720209895, 299792.458 * 86400.0 / 149597870.7,
+                   84381.406 / 3600.0 * kPi / 180.0);
+  for (auto& ev : c->ev) {
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+      snprintf(g_create_error, sizeof g_create_error, "cudaEventCreate failed");
+      delete c;
+      return NDT_ECUDA;
+    }
+  }
+  if (c->counters.ensure(64) != cudaSuccess || c->queue_head.ensure(64) != cudaSuccess) {
+    snprintf(g_create_error, sizeof g_create_error, "device allocation failed");
+    delete c;
+    return NDT_ENOMEM;
+  }
+  cudaMemset(c->counters.p, 0, 64);
+  *out = c;
+  return NDT_OK;
+}
+
+void ndt_destroy(ndt_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  DevBuf* bufs[] = {&c->ex_dev, &c->pos_to_table_dev, &c->planes, &c->planes_tmp, &c->jobs_dev,
+                    &c->absmax_dev, &c->scales_dev, &c->stage_images, &c->stage_vars,
+                    &c->stage_states, &c->snr, &c->out_tmp, &c->xy_tmp, &c->fam_orb_off,
+                    &c->fam_exp_off, &c->fam_exp_pos, &c->item_off, &c->fam_order,
+                    &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out};
+  for (DevBuf* b : bufs) b->release();
+  delete c;
+}
+
+const char* ndt_last_error(const ndt_ctx* c) { return c ? c->err.c_str() : g_create_error; }
+
+ndt_status ndt_set_constants(ndt_ctx* ctx, double gm, double c_light, double obliquity_rad) {
+  if (!ctx) return NDT_EINVAL;
+  if (!std::isfinite(gm) || !std::isfinite(c_light) || !std::isfinite(obliquity_rad))
+    return fail(ctx, NDT_EINVAL, "constants must be finite");
+  set_default_phys(ctx, gm, c_light, obliquity_rad);
+  if (ctx->n_exp > 0) {   // the projection rows depend on the obliquity
+    for (int s = 0; s < ctx->n_exp; ++s)
+      derive_projection(ctx->table[ctx->sorted_to_table[s]], ctx->obliquity, ctx->ex_host[s]);
+    NDT_CK(cudaMemcpyAsync(ctx->ex_dev.p, ctx->ex_host.data(), sizeof(ExpDev) * ctx->n_exp,
+                           cudaMemcpyHostToDevice, ctx->stream), "exposure upload");
+    NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  }
+  return NDT_OK;
+}
+
+ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_exp,
+                              const float* const* images, const float* const* variances,
+                              int32_t plane_dtype) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!meta || !images || n_exp < 1 || n_exp > 65535)
+    return fail(ctx, NDT_EINVAL, "meta/images null or n_exp outside [1, 65535]");
+  if (plane_dtype < 0 || plane_dtype > 2) return fail(ctx, NDT_EINVAL, "bad plane dtype %d", plane_dtype);
+  for (int j = 0; j < n_exp; ++j) {
+    const ndt_exposure& m = meta[j];
+    const double det = m.cd[0] * m.cd[3] - m.cd[1] * m.cd[2];
+    if (!images[j]) return fail(ctx, NDT_EINVAL, "image %d is null", j);
+    if (!std::isfinite(m.mjd)) return fail(ctx, NDT_EINVAL, "exposure %d: epoch not finite", j);
+    if (!(m.psf_sigma_px > 0.0f && m.psf_sigma_px <= 4.0f))
+      return fail(ctx, NDT_EINVAL, "exposure %d: psf sigma %g outside (0, 4]", j, m.psf_sigma_px);
+    if (!variances && !(m.variance > 0.0f))
+      return fail(ctx, NDT_EINVAL, "exposure %d: variance must be > 0", j);
+    if (!(std::isfinite(det) && det != 0.0)) return fail(ctx, NDT_EINVAL, "exposure %d: singular CD", j);
+    if (m.width < 1 || m.height < 1 || m.width > 32768 || m.height > 32768)
+      return fail(ctx, NDT_EINVAL, "exposure %d: size %dx%d", j, m.width, m.height);
+    if (variances && !variances[j]) return fail(ctx, NDT_EINVAL, "variance plane %d is null", j);
+  }
+  ctx->n_exp = 0;
+  ctx->table.assign(meta, meta + n_exp);
+  ctx->sorted_to_table.resize(n_exp);
+  std::iota(ctx->sorted_to_table.begin(), ctx->sorted_to_table.end(), 0);
+  std::stable_sort(ctx->sorted_to_table.begin(), ctx->sorted_to_table.end(),
+                   [&](int a, int b) { return meta[a].mjd < meta[b].mjd; });
+  ctx->table_to_sorted.assign(n_exp, 0);
+  for (int s = 0; s < n_exp; ++s) ctx->table_to_sorted[ctx->sorted_to_table[s]] = s;
+
+  // plane layout (sorted order), staging of host images
+  ctx->ex_host.assign(n_exp, ExpDev{});
+  std::vector<PlaneJob> jobs(n_exp);
+  int64_t plane_elems = 0, img_elems = 0;
+  int max_tiles = 0;
+  for (int s = 0; s < n_exp; ++s) {
+    const ndt_exposure& m = meta[ctx->sorted_to_table[s]];
+    ExpDev& e = ctx->ex_host[s];
+    e.t = m.mjd;
+    for (int i = 0; i < 3; ++i) e.obs[i] = m.obs_xyz[i];
+    derive_projection(m, ctx->obliquity, e);
+    e.W = m.width;
+    e.H = m.height;
+    e.tiles_x = (m.width + kTile - 1) / kTile;
+    const int tiles_y = (m.height + kTile - 1) / kTile;
+    e.plane_off = plane_elems;
+    e.s_psi = 1.0f;
+    e.s_phi = 1.0f;
+    plane_elems += (int64_t)e.tiles_x * tiles_y * kTile * kTile;
+    max_tiles = std::max(max_tiles, e.tiles_x * tiles_y);
+    PlaneJob& J = jobs[s];
+    J.var_c = m.variance > 0.0f ? m.variance : 1.0f;
+    J.sigma = m.psf_sigma_px;
+    J.W = m.width;
+    J.H = m.height;
+    J.tiles_x = e.tiles_x;
+    J.tiles_y = tiles_y;
+    J.plane_off = e.plane_off;
+    img_elems += (int64_t)m.width * m.height;
+  }
+  // images: device pointers are used in place, host images are staged
+  bool any_host_img = false, any_host_var = false;
+  for (int j = 0; j < n_exp; ++j) {
+    if (!is_device_ptr(images[j])) any_host_img = true;
+    if (variances && !is_device_ptr(variances[j])) any_host_var = true;
+  }
+  if (any_host_img) NDT_CK(ctx->stage_images.ensure(sizeof(float) * img_elems), "image staging");
+  if (any_host_var) NDT_CK(ctx->stage_vars.ensure(sizeof(float) * img_elems), "variance staging");
+  int64_t img_off = 0;
+  for (int s = 0; s < n_exp; ++s) {
+    const int j = ctx->sorted_to_table[s];
+    const size_t bytes = sizeof(float) * (size_t)meta[j].width * meta[j].height;
+    PlaneJob& J = jobs[s];
+    if (is_device_ptr(images[j])) {
+      J.image = images[j];
+    } else {
+      float* dst = ctx->stage_images.as<float>() + img_off;
+      NDT_CK(cudaMemcpyAsync(dst, images[j], bytes, cudaMemcpyHostToDevice, ctx->stream), "image H2D");
+      J.image = dst;
+    }
+    J.var = nullptr;
+    if (variances) {
+      if (is_device_ptr(variances[j])) {
+        J.var = variances[j];
+      } else {
+        float* dst = ctx->stage_vars.as<float>() + img_off;
+        NDT_CK(cudaMemcpyAsync(dst, variances[j], bytes, cudaMemcpyHostToDevice, ctx->stream),
+               "variance H2D");
+        J.var = dst;
+      }
+    }
+    img_off += (int64_t)meta[j].width * meta[j].height;
+  }
+  NDT_CK(ctx->jobs_dev.ensure(sizeof(PlaneJob) * n_exp), "job table");
+  NDT_CK(cudaMemcpyAsync(ctx->jobs_dev.p, jobs.data(), sizeof(PlaneJob) * n_exp,
+                         cudaMemcpyHostToDevice, ctx->stream), "job upload");
+  const size_t pair_bytes = plane_dtype == NDT_PLANE_F32 ? 8 : 4;
+  NDT_CK(ctx->planes.ensure(pair_bytes * plane_elems), "plane allocation");
+  float2* f32 = nullptr;
+  if (plane_dtype == NDT_PLANE_F32) {
+    f32 = ctx->planes.as<float2>();
+  } else {
+    NDT_CK(ctx->planes_tmp.ensure(8 * plane_elems), "FP32 plane scratch");
+    f32 = ctx->planes_tmp.as<float2>();
+  }
+  record(ctx, 0);
+  NDT_CK(launch_planes_f32(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, f32, ctx->stream),
+         "plane kernel");
+  ctx->launches += 1;
+  if (plane_dtype != NDT_PLANE_F32) {
+    NDT_CK(ctx->absmax_dev.ensure(8 * n_exp), "absmax");
+    NDT_CK(ctx->scales_dev.ensure(8 * n_exp), "scales");
+    NDT_CK(cudaMemsetAsync(ctx->absmax_dev.p, 0, 8 * n_exp, ctx->stream), "memset");
+    NDT_CK(launch_plane_absmax(ctx->jobs_dev.as<PlaneJob>(), n_exp, f32,
+                               ctx->absmax_dev.as<unsigned int>(), ctx->stream), "absmax kernel");
+    NDT_CK(launch_plane_quantize(ctx->jobs_dev.as<PlaneJob>(), n_exp, f32,
+                                 ctx->absmax_dev.as<unsigned int>(), plane_dtype, ctx->planes.p,
+                                 ctx->scales_dev.as<float>(), ctx->stream), "quantize kernel");
+    ctx->launches += 2;
+  }
+  record(ctx, 1);
+  ctx->have_planes_ev = true;
+  if (plane_dtype != NDT_PLANE_F32) {
+    std::vector<float> sc(2 * n_exp);
+    NDT_CK(cudaMemcpyAsync(sc.data(), ctx->scales_dev.p, 8 * n_exp, cudaMemcpyDeviceToHost,
+                           ctx->stream), "scale read-back");
+    NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+    for (int s = 0; s < n_exp; ++s) {
+      ctx->ex_host[s].s_psi = sc[2 * s];
+      ctx->ex_host[s].s_phi = sc[2 * s + 1];
+    }
+  }
+  NDT_CK(ctx->ex_dev.ensure(sizeof(ExpDev) * n_exp), "exposure table");
+  NDT_CK(cudaMemcpyAsync(ctx->ex_dev.p, ctx->ex_host.data(), sizeof(ExpDev) * n_exp,
+                         cudaMemcpyHostToDevice, ctx->stream), "exposure upload");
+  NDT_CK(ctx->pos_to_table_dev.ensure(4 * n_exp), "permutation");
+  NDT_CK(cudaMemcpyAsync(ctx->pos_to_table_dev.p, ctx->sorted_to_table.data(), 4 * n_exp,
+                         cudaMemcpyHostToDevice, ctx->stream), "permutation upload");
+  // host vectors above must outlive the async copies
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->plane_type = plane_dtype;
+  ctx->n_exp = n_exp;
+  ctx->last_n = 0;
+  return NDT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Families on the host: validate, map exposures to sorted positions (epoch
+// order within each family), build the queue order (families with more
+// exposures first) and upload.
+ndt_status prepare_families(ndt_ctx* ctx, int64_t n, const int64_t* fo_in, const int64_t* fe_in,
+                            const int32_t* fi_in, int32_t n_fam, bool need_queue, int team,
+                            StackArgs& a) {
+  std::vector<int64_t> fo, fe;
+  std::vector<int32_t> fi;
+  if (n_fam > 0) {
+    if (!fo_in || !fe_in || !fi_in) return fail(ctx, NDT_EINVAL, "family arrays must be non-null");
+    fo.resize(n_fam + 1);
+    fe.resize(n_fam + 1);
+    auto fetch = [&](const void* src, void* dst, size_t bytes) -> cudaError_t {
+      if (is_device_ptr(src)) return cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+      std::memcpy(dst, src, bytes);
+      return cudaSuccess;
+    };
+    NDT_CK(fetch(fo_in, fo.data(), 8 * (n_fam + 1)), "family offsets");
+    NDT_CK(fetch(fe_in, fe.data(), 8 * (n_fam + 1)), "family exposure offsets");
+    if (fo[0] != 0 || fo[n_fam] != n) return fail(ctx, NDT_EINVAL, "family orbit offsets must span [0, n)");
+    if (fe[0] != 0) return fail(ctx, NDT_EINVAL, "family exposure offsets must start at 0");
+    for (int f = 0; f < n_fam; ++f)
+      if (fo[f + 1] < fo[f] || fe[f + 1] < fe[f]) return fail(ctx, NDT_EINVAL, "offsets decrease at %d", f);
+    fi.resize(fe[n_fam]);
+    if (!fi.empty()) NDT_CK(fetch(fi_in, fi.data(), 4 * fi.size()), "family exposure list");
+    std::vector<unsigned char> seen(ctx->n_exp, 0);
+    for (int f = 0; f < n_fam; ++f) {
+      for (int64_t k = fe[f]; k < fe[f + 1]; ++k) {
+        const int32_t j = fi[k];
+        if (j < 0 || j >= ctx->n_exp) return fail(ctx, NDT_EINVAL, "family %d: exposure %d out of range", f, j);
+        if (seen[j]) return fail(ctx, NDT_EINVAL, "family %d: exposure %d repeated", f, j);
+        seen[j] = 1;
+        fi[k] = ctx->table_to_sorted[j];
+      }
+      for (int64_t k = fe[f]; k < fe[f + 1]; ++k) seen[ctx->sorted_to_table[fi[k]]] = 0;
+      std::sort(fi.begin() + fe[f], fi.begin() + fe[f + 1]);
+    }
+  } else if (need_queue) {
+    n_fam = 1;
+    fo = {0, n};
+    fe = {0, (int64_t)ctx->n_exp};
+    fi.resize(ctx->n_exp);
+    std::iota(fi.begin(), fi.end(), 0);
+  }
+  a.n_fam = n_fam;
+  a.fam_orb_off = a.fam_exp_off = nullptr;
+  a.fam_exp_pos = nullptr;
+  a.item_off = nullptr;
+  a.fam_order = nullptr;
+  a.n_items = 0;
+  ctx->samples = 0;
+  if (n_fam == 0) {
+    ctx->samples = n * (int64_t)ctx->n_exp;
+    return NDT_OK;
+  }
+  for (int f = 0; f < n_fam; ++f) ctx->samples += (fo[f + 1] - fo[f]) * (fe[f + 1] - fe[f]);
+  NDT_CK(ctx->fam_orb_off.ensure(8 * (n_fam + 1)), "family buffers");
+  NDT_CK(ctx->fam_exp_off.ensure(8 * (n_fam + 1)), "family buffers");
+  NDT_CK(ctx->fam_exp_pos.ensure(4 * std::max<size_t>(fi.size(), 1)), "family buffers");
+  NDT_CK(cudaMemcpyAsync(ctx->fam_orb_off.p, fo.data(), 8 * (n_fam + 1), cudaMemcpyHostToDevice, ctx->stream), "upload");
+  NDT_CK(cudaMemcpyAsync(ctx->fam_exp_off.p, fe.data(), 8 * (n_fam + 1), cudaMemcpyHostToDevice, ctx->stream), "upload");
+  if (!fi.empty())
+    NDT_CK(cudaMemcpyAsync(ctx->fam_exp_pos.p, fi.data(), 4 * fi.size(), cudaMemcpyHostToDevice, ctx->stream), "upload");
+  a.fam_orb_off = ctx->fam_orb_off.as<int64_t>();
+  a.fam_exp_off = ctx->fam_exp_off.as<int64_t>();
+  a.fam_exp_pos = ctx->fam_exp_pos.as<int32_t>();
+  std::vector<int64_t> item_off;
+  std::vector<int32_t> order;
+  if (need_queue) {
+    order.resize(n_fam);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+      return (fe[x + 1] - fe[x]) > (fe[y + 1] - fe[y]);
+    });
+    item_off.resize(n_fam + 1);
+    item_off[0] = 0;
+    for (int q = 0; q < n_fam; ++q) {
+      const int f = order[q];
+      item_off[q + 1] = item_off[q] + (fo[f + 1] - fo[f] + team - 1) / team;
+    }
+    NDT_CK(ctx->item_off.ensure(8 * (n_fam + 1)), "queue buffers");
+    NDT_CK(ctx->fam_order.ensure(4 * n_fam), "queue buffers");
+    NDT_CK(cudaMemcpyAsync(ctx->item_off.p, item_off.data(), 8 * (n_fam + 1), cudaMemcpyHostToDevice, ctx->stream), "upload");
+    NDT_CK(cudaMemcpyAsync(ctx->fam_order.p, order.data(), 4 * n_fam, cudaMemcpyHostToDevice, ctx->stream), "upload");
+    a.item_off = ctx->item_off.as<int64_t>();
+    a.fam_order = ctx->fam_order.as<int32_t>();
+    a.n_items = item_off[n_fam];
+  }
+  // the host vectors are released on return: wait for their uploads
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
+  if (ctx->mode == NDT_LAUNCH_PLAIN) {
+    NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+    record(ctx, 2);
+    NDT_CK(launch_stack_plain(a, ctx->stream), "stack kernel");
+    record(ctx, 3);
+    ctx->launches += 1;
+    ctx->have_stack_ev = true;
+    return NDT_OK;
+  }
+  a.queue_head = ctx->queue_head.as<unsigned long long>();
+  auto enqueue = [&]() -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(ctx->queue_head.p, 0, 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream);
+    if (e == cudaSuccess) e = launch_stack_persistent(a, ctx->n_sms, ctx->stream);
+    return e;
+  };
+  if (ctx->use_graph) {
+    std::vector<unsigned char> key(sizeof(StackArgs) + 8);
+    std::memcpy(key.data(), &a, sizeof(StackArgs));
+    const int64_t extra = ((int64_t)ctx->orbit_tile << 32) | ctx->exp_tile;
+    std::memcpy(key.data() + sizeof(StackArgs), &extra, 8);
+    if (!ctx->graph || key != ctx->graph_key) {
+      if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+      cudaGraph_t g;
+      NDT_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "capture begin");
+      cudaError_t e = enqueue();
+      cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "captured stack");
+      NDT_CK(e2, "capture end");
+      NDT_CK(cudaGraphInstantiate(&ctx->graph, g, 0), "graph instantiate");
+      cudaGraphDestroy(g);
+      ctx->graph_key = key;
+    }
+    record(ctx, 2);
+    NDT_CK(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
+    record(ctx, 3);
+  } else {
+    record(ctx, 2);
+    NDT_CK(enqueue(), "persistent stack");
+    record(ctx, 3);
+  }
+  ctx->launches += 1;
+  ctx->have_stack_ev = true;
+  return NDT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                            const int64_t* fam_orbit_off, const int64_t* fam_exp_off,
+                            const int32_t* fam_exp_idx, int32_t n_fam, int32_t min_obs,
+                            float* psi_sum, float* phi_sum, int32_t* nobs, float* snr) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "stack_orbits before load_exposures");
+  if (n_orbits < 0 || n_orbits > 0xffffffffll) return fail(ctx, NDT_EINVAL, "n_orbits %lld out of range", (long long)n_orbits);
+  if (n_orbits > 0 && !states) return fail(ctx, NDT_EINVAL, "states is null");
+  if (n_fam < 0) return fail(ctx, NDT_EINVAL, "n_fam < 0");
+  if (!std::isfinite(t0)) return fail(ctx, NDT_EINVAL, "t0 not finite");
+  StackArgs a{};
+  const bool persistent = ctx->mode == NDT_LAUNCH_PERSISTENT;
+  ndt_status s = prepare_families(ctx, n_orbits, fam_orbit_off, fam_exp_off, fam_exp_idx, n_fam,
+                                  persistent, ctx->orbit_tile, a);
+  if (s != NDT_OK) return s;
+  ctx->last_n = 0;
+  if (n_orbits == 0) return NDT_OK;
+  const void* st_dev = nullptr;
+  s = to_device(ctx, states, sizeof(double) * 6 * n_orbits, ctx->stage_states, &st_dev);
+  if (s != NDT_OK) return s;
+  NDT_CK(ctx->snr.ensure(4 * n_orbits), "snr buffer");
+  // host outputs go through a device scratch of 3 arrays
+  const bool h_psi = psi_sum && !is_device_ptr(psi_sum), h_phi = phi_sum && !is_device_ptr(phi_sum);
+  const bool h_nobs = nobs && !is_device_ptr(nobs), h_snr = snr && !is_device_ptr(snr);
+  if (h_psi || h_phi || h_nobs) NDT_CK(ctx->out_tmp.ensure(12 * n_orbits), "output scratch");
+  a.states = static_cast<const double*>(st_dev);
+  a.n = n_orbits;
+  a.t0 = t0;
+  a.ex = ctx->ex_dev.as<ExpDev>();
+  a.n_exp = ctx->n_exp;
+  a.planes = ctx->planes.p;
+  a.plane_type = ctx->plane_type;
+  a.orbit_tile = ctx->orbit_tile;
+  a.exp_tile = ctx->exp_tile;
+  a.psi_sum = h_psi ? ctx->out_tmp.as<float>() : psi_sum;
+  a.phi_sum = h_phi ? ctx->out_tmp.as<float>() + n_orbits : phi_sum;
+  a.nobs = h_nobs ? reinterpret_cast<int32_t*>(ctx->out_tmp.as<float>() + 2 * n_orbits) : nobs;
+  a.snr = ctx->snr.as<float>();
+  a.min_obs = min_obs;
+  a.counters = ctx->counters.as<unsigned long long>();
+  a.ph = ctx->ph;
+  s = run_stack(ctx, a);
+  if (s != NDT_OK) return s;
+  ctx->last_n = n_orbits;
+  if (snr && !h_snr)
+    NDT_CK(cudaMemcpyAsync(snr, ctx->snr.p, 4 * n_orbits, cudaMemcpyDeviceToDevice, ctx->stream), "snr copy");
+  if (h_psi || h_phi || h_nobs || h_snr) {
+    if (h_psi) NDT_CK(cudaMemcpyAsync(psi_sum, a.psi_sum, 4 * n_orbits, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    if (h_phi) NDT_CK(cudaMemcpyAsync(phi_sum, a.phi_sum, 4 * n_orbits, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    if (h_nobs) NDT_CK(cudaMemcpyAsync(nobs, a.nobs, 4 * n_orbits, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    if (h_snr) NDT_CK(cudaMemcpyAsync(snr, ctx->snr.p, 4 * n_orbits, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+    NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+    unsigned long long cnt[2];
+    NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 16, cudaMemcpyDeviceToHost), "counters");
+    if (cnt[1]) return fail(ctx, NDT_ENOCONV, "%llu Kepler solves did not converge", cnt[1]);
+  }
+  return NDT_OK;
+}
+
+ndt_status ndt_topk_candidates(ndt_ctx* ctx, int64_t k, int64_t* idx_out, float* snr_out,
+                               int64_t* k_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->last_n <= 0) return fail(ctx, NDT_ESTATE, "topk_candidates without a stacked batch");
+  if (k < 0) return fail(ctx, NDT_EINVAL, "k < 0");
+  const int64_t n = ctx->last_n;
+  if (k > n) k = n;
+  if (k_out) *k_out = k;
+  if (k == 0) return NDT_OK;
+  if (k > 8192) return fail(ctx, NDT_EINVAL, "k = %lld above the supported 8192", (long long)k);
+  const size_t sb = topk_scratch_bytes(n, k);
+  NDT_CK(ctx->topk_scratch.ensure(sb), "top-k scratch");
+  const bool h_idx = idx_out && !is_device_ptr(idx_out), h_snr = snr_out && !is_device_ptr(snr_out);
+  if (h_idx || h_snr) NDT_CK(ctx->topk_out.ensure(12 * k), "top-k output scratch");
+  int64_t* di = h_idx ? ctx->topk_out.as<int64_t>() : idx_out;
+  float* ds = h_snr ? reinterpret_cast<float*>(ctx->topk_out.as<int64_t>() + k) : snr_out;
+  int L = 0;
+  record(ctx, 4);
+  NDT_CK(launch_topk(ctx->snr.as<float>(), n, k, ctx->topk_scratch.p, ctx->topk_scratch.cap, di, ds,
+                     &L, ctx->stream), "top-k kernels");
+  record(ctx, 5);
+  ctx->have_topk_ev = true;
+  ctx->launches += L;
+  if (h_idx) NDT_CK(cudaMemcpyAsync(idx_out, di, 8 * k, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  if (h_snr) NDT_CK(cudaMemcpyAsync(snr_out, ds, 4 * k, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status ndt_predict_positions(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                                 double* xy_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "predict_positions before load_exposures");
+  if (n_orbits < 0 || (n_orbits > 0 && (!states || !xy_out)))
+    return fail(ctx, NDT_EINVAL, "bad arguments");
+  if (n_orbits == 0) return NDT_OK;
+  const void* st_dev = nullptr;
+  ndt_status s = to_device(ctx, states, sizeof(double) * 6 * n_orbits, ctx->stage_states, &st_dev);
+  if (s != NDT_OK) return s;
+  const size_t bytes = sizeof(double) * 2 * (size_t)n_orbits * ctx->n_exp;
+  const bool host_out = !is_device_ptr(xy_out);
+  double* dst = xy_out;
+  if (host_out) {
+    NDT_CK(ctx->xy_tmp.ensure(bytes), "position scratch");
+    dst = ctx->xy_tmp.as<double>();
+  }
+  NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+  NDT_CK(launch_predict(static_cast<const double*>(st_dev), n_orbits, t0, ctx->ex_dev.as<ExpDev>(),
+                        ctx->pos_to_table_dev.as<int32_t>(), ctx->n_exp, ctx->ph, dst,
+                        ctx->counters.as<unsigned long long>(), ctx->stream), "predict kernel");
+  ctx->launches += 1;
+  if (host_out) NDT_CK(cudaMemcpyAsync(xy_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  unsigned long long cnt[2];
+  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 16, cudaMemcpyDeviceToHost), "counters");
+  if (cnt[1]) return fail(ctx, NDT_ENOCONV, "%llu Kepler solves did not converge", cnt[1]);
+  return NDT_OK;
+}
+
+ndt_status ndt_get_planes(ndt_ctx* ctx, int32_t j, float* psi_out, float* phi_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "no exposures loaded");
+  if (j < 0 || j >= ctx->n_exp) return fail(ctx, NDT_EINVAL, "exposure %d out of range", j);
+  const ExpDev& e = ctx->ex_host[ctx->table_to_sorted[j]];
+  const size_t bytes = sizeof(float) * (size_t)e.W * e.H;
+  const bool hp = psi_out && !is_device_ptr(psi_out), hf = phi_out && !is_device_ptr(phi_out);
+  if (hp || hf) NDT_CK(ctx->xy_tmp.ensure(2 * bytes), "decode scratch");
+  float* dp = hp ? ctx->xy_tmp.as<float>() : psi_out;
+  float* df = hf ? ctx->xy_tmp.as<float>() + (size_t)e.W * e.H : phi_out;
+  NDT_CK(launch_plane_decode(ctx->planes.p, ctx->plane_type, &e, dp, df, ctx->stream), "decode kernel");
+  ctx->launches += 1;
+  if (hp) NDT_CK(cudaMemcpyAsync(psi_out, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  if (hf) NDT_CK(cudaMemcpyAsync(phi_out, df, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status ndt_set_launch(ndt_ctx* ctx, int32_t mode, int32_t orbit_tile, int32_t exp_tile,
+                          int32_t use_graph) {
+  if (!ctx) return NDT_EINVAL;
+  if (mode != NDT_LAUNCH_PLAIN && mode != NDT_LAUNCH_PERSISTENT)
+    return fail(ctx, NDT_EINVAL, "bad launch mode %d", mode);
+  if (mode == NDT_LAUNCH_PERSISTENT) {
+    if (orbit_tile != 32 && orbit_tile != 64 && orbit_tile != 128)
+      return fail(ctx, NDT_EINVAL, "orbit_tile %d not in {32, 64, 128}", orbit_tile);
+    if (exp_tile != 8 && exp_tile != 16 && exp_tile != 32)
+      return fail(ctx, NDT_EINVAL, "exp_tile %d not in {8, 16, 32}", exp_tile);
+    ctx->orbit_tile = orbit_tile;
+    ctx->exp_tile = exp_tile;
+  }
+  ctx->mode = mode;
+  ctx->use_graph = use_graph ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_autotune(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                        const int64_t* fam_orbit_off, const int64_t* fam_exp_off,
+                        const int32_t* fam_exp_idx, int32_t n_fam, float* times_ms) {
+  if (!ctx) return NDT_EINVAL;
+  const int32_t saved_mode = ctx->mode, saved_graph = ctx->use_graph;
+  const int ots[3] = {32, 64, 128}, ets[3] = {8, 16, 32};
+  float best = 1e30f;
+  int best_ot = 64, best_et = 16;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      ctx->mode = NDT_LAUNCH_PERSISTENT;
+      ctx->orbit_tile = ots[i];
+      ctx->exp_tile = ets[j];
+      ctx->use_graph = 0;
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+        ndt_status s = ndt_stack_orbits(ctx, states, t0, n_orbits, fam_orbit_off, fam_exp_off,
+                                        fam_exp_idx, n_fam, 1, nullptr, nullptr, nullptr, nullptr);
+        if (s != NDT_OK) { ctx->mode = saved_mode; ctx->use_graph = saved_graph; return s; }
+        NDT_CK(cudaEventSynchronize(ctx->ev[3]), "sync");
+        float ms = 0.0f;
+        NDT_CK(cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]), "timing");
+        if (rep > 0) ms_best = std::min(ms_best, ms);
+      }
+      if (times_ms) times_ms[3 * i + j] = ms_best;
+      if (ms_best < best) { best = ms_best; best_ot = ots[i]; best_et = ets[j]; }
+    }
+  ctx->mode = saved_mode;
+  ctx->use_graph = saved_graph;
+  ctx->orbit_tile = best_ot;
+  ctx->exp_tile = best_et;
+  return NDT_OK;
+}
+
+ndt_status ndt_get_stats(ndt_ctx* ctx, ndt_stats* out) {
+  if (!ctx || !out) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  std::memset(out, 0, sizeof *out);
+  unsigned long long cnt[2];
+  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 16, cudaMemcpyDeviceToHost), "counters");
+  out->kernel_launches = ctx->launches;
+  out->samples = ctx->samples;
+  out->valid_samples = (int64_t)cnt[0];
+  out->kepler_failures = (int64_t)cnt[1];
+  if (ctx->have_stack_ev) cudaEventElapsedTime(&out->last_stack_ms, ctx->ev[2], ctx->ev[3]);
+  if (ctx->have_planes_ev) cudaEventElapsedTime(&out->last_planes_ms, ctx->ev[0], ctx->ev[1]);
+  if (ctx->have_topk_ev) cudaEventElapsedTime(&out->last_topk_ms, ctx->ev[4], ctx->ev[5]);
+  out->orbit_tile = ctx->orbit_tile;
+  out->exp_tile = ctx->exp_tile;
+  out->launch_mode = ctx->mode;
+  out->plane_dtype = ctx->plane_type;
+  return NDT_OK;
+}
+
+ndt_status ndt_synchronize(ndt_ctx* ctx) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+}  // extern "C"

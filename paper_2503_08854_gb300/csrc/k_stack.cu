@@ -1,0 +1,261 @@
+// k_stack.cu -- the stacking hot path (paper Algorithm 1: SearchImages,
+// FilterGPUIntersections, FindLocalSignal and the constant-flux combination,
+// fused into one pass that never materialises an intersection).
+//
+// One thread owns one orbit and walks its exposures in epoch order.  The
+// orbit state is carried from one exposure epoch to the next by a two-body
+// step (universal variables), so consecutive steps are short and their
+// Stumpff functions are low-order polynomials; the light-time correction is
+// a second-order expansion about the geometric state.  Psi, Phi and the
+// sample count live in registers (compensated FP32 sums) and the stacked
+// statistic is formed in the epilogue.  The FP64 pipe bounds this kernel;
+// the gathers move 8 bytes (FP32 planes) or 4 bytes (BF16/FP16) per valid
+// sample.
+#include "ndt_internal.cuh"
+
+namespace ndt {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ void load_state(const double* __restrict__ s, int64_t n, int64_t o,
+                                           double r[3], double v[3]) {
+  for (int c = 0; c < 3; ++c) {
+    r[c] = __ldg(s + c * n + o);
+    v[c] = __ldg(s + (c + 3) * n + o);
+  }
+}
+
+__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* __restrict__ a, int64_t n,
+                                                   int64_t key) {
+  int64_t lo = 0, hi = n;  // first index with a[i] > key
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Per-thread walk state.
+struct Walk {
+  double r[3], v[3], rn, inv_r, t_prev;
+  OrbitConst oc;
+  CSum sp, sf;
+  int cnt;
+  bool failed;
+};
+
+__device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double* __restrict__ states,
+                                          int64_t n, int64_t o, double t0) {
+  load_state(states, n, o, w.r, w.v);
+  w.rn = sqrt(w.r[0] * w.r[0] + w.r[1] * w.r[1] + w.r[2] * w.r[2]);
+  w.inv_r = 1.0 / w.rn;
+  w.oc = orbit_const(ph, w.r, w.v, w.inv_r);
+  w.t_prev = t0;
+  w.sp = CSum{0.0f, 0.0f};
+  w.sf = CSum{0.0f, 0.0f};
+  w.cnt = 0;
+  w.failed = false;
+}
+
+template <int PT>
+__device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDev& e,
+                                            const void* __restrict__ planes) {
+  if (w.failed) return;
+  const double dt = e.t - w.t_prev;
+  if (kepler_step(ph, w.oc, dt, w.r, w.v, w.rn, w.inv_r) < 0) {
+    w.failed = true;
+    return;
+  }
+  w.t_prev = e.t;
+  double rho[3], x, y;
+  apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
+  int ix, iy;
+  if (project(e, rho, x, y) && nearest_pixel(e, x, y, ix, iy)) {
+    const float2 pv = gather_plane<PT>(planes, e, ix, iy);
+    w.sp.add(pv.x);
+    w.sf.add(pv.y);
+    w.cnt += 1;
+  }
+}
+
+__device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, int64_t o,
+                                            bool active) {
+  int valid = 0, fails = 0;
+  if (active) {
+    const float P = w.sp.value(), F = w.sf.value();
+    if (a.psi_sum) a.psi_sum[o] = P;
+    if (a.phi_sum) a.phi_sum[o] = F;
+    if (a.nobs) a.nobs[o] = w.cnt;
+    float nu = -INFINITY;
+    if (!w.failed && F > 0.0f && w.cnt >= a.min_obs) nu = __fdiv_rn(P, __fsqrt_rn(F));
+    if (!(nu == nu)) nu = -INFINITY;
+    a.snr[o] = nu;
+    valid = w.cnt;
+    fails = w.failed ? 1 : 0;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    valid += __shfl_xor_sync(0xffffffffu, valid, off);
+    fails += __shfl_xor_sync(0xffffffffu, fails, off);
+  }
+  if ((threadIdx.x & 31) == 0 && a.counters) {
+    if (valid) atomicAdd(a.counters + 0, (unsigned long long)valid);
+    if (fails) atomicAdd(a.counters + 1, (unsigned long long)fails);
+  }
+}
+
+// Plain form: one thread per orbit, grid covers all orbits.
+template <int PT>
+__global__ void __launch_bounds__(kBlock) k_stack_plain(const StackArgs a) {
+  const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const bool active = o < a.n;
+  Walk w;
+  if (active) {
+    walk_init(w, a.ph, a.states, a.n, o, a.t0);
+    int64_t e_begin = 0, e_end = a.n_exp;
+    if (a.n_fam > 0) {
+      const int64_t f = upper_bound_i64(a.fam_orb_off, a.n_fam + 1, o) - 1;
+      e_begin = __ldg(a.fam_exp_off + f);
+      e_end = __ldg(a.fam_exp_off + f + 1);
+    }
+    for (int64_t k = e_begin; k < e_end; ++k) {
+      const int j = a.n_fam > 0 ? __ldg(a.fam_exp_pos + k) : (int)k;
+      walk_sample<PT>(w, a.ph, a.ex[j], a.planes);
+    }
+  }
+  walk_finish(w, a, o, active);
+}
+
+__device__ __forceinline__ void team_sync(int team, int team_threads) {
+  if (team_threads == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(team_threads) : "memory");
+  }
+}
+
+// Persistent form: teams of TEAM_WARPS warps pop (family, orbit tile) items
+// from a global counter in longest-family-first order; each team stages ET
+// exposure records at a time in shared memory and walks its orbits through
+// them.  The loop ends when the counter passes the last item: no thread ever
+// waits on another team.
+template <int PT, int TEAM_WARPS, int ET>
+__global__ void __launch_bounds__(kBlock) k_stack_persistent(const StackArgs a) {
+  constexpr int TEAM = TEAM_WARPS * 32;
+  constexpr int NTEAMS = kBlock / TEAM;
+  __shared__ ExpDev stage[NTEAMS][ET];
+  __shared__ long long item_sh[NTEAMS];
+  const int team = threadIdx.x / TEAM;
+  const int tl = threadIdx.x % TEAM;
+  for (;;) {
+    if (tl == 0) item_sh[team] = (long long)atomicAdd(a.queue_head, 1ull);
+    team_sync(team, TEAM);
+    const long long item = item_sh[team];
+    if (item >= a.n_items) break;
+    const int64_t fq = upper_bound_i64(a.item_off, a.n_fam + 1, item) - 1;
+    const int f = __ldg(a.fam_order + fq);
+    const int64_t tile = item - __ldg(a.item_off + fq);
+    const int64_t o_begin = __ldg(a.fam_orb_off + f), o_end = __ldg(a.fam_orb_off + f + 1);
+    const int64_t o = o_begin + tile * TEAM + tl;
+    const bool active = o < o_end;
+    const int64_t e_begin = __ldg(a.fam_exp_off + f), e_end = __ldg(a.fam_exp_off + f + 1);
+    Walk w;
+    if (active) walk_init(w, a.ph, a.states, a.n, o, a.t0);
+    for (int64_t eb = e_begin; eb < e_end; eb += ET) {
+      const int cnt = (int)min((int64_t)ET, e_end - eb);
+      // stage cnt exposure records (19 doubles each) into shared memory
+      double* dst = reinterpret_cast<double*>(&stage[team][0]);
+      for (int i = tl; i < cnt * 19; i += TEAM) {
+        const int jj = i / 19, wd = i % 19;
+        const int j = __ldg(a.fam_exp_pos + eb + jj);
+        dst[i] = __ldg(reinterpret_cast<const double*>(a.ex + j) + wd);
+      }
+      team_sync(team, TEAM);
+      if (active)
+        for (int jj = 0; jj < cnt; ++jj) walk_sample<PT>(w, a.ph, stage[team][jj], a.planes);
+      team_sync(team, TEAM);
+    }
+    walk_finish(w, a, o, active);
+    team_sync(team, TEAM);   // every thread has read item_sh before it is rewritten
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_predict(const double* __restrict__ states, int64_t n,
+                                                   double t0, const ExpDev* __restrict__ ex,
+                                                   const int32_t* __restrict__ pos_to_table,
+                                                   int32_t n_exp, Phys ph, double* __restrict__ xy,
+                                                   unsigned long long* counters) {
+  const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (o >= n) return;
+  Walk w;
+  walk_init(w, ph, states, n, o, t0);
+  for (int j = 0; j < n_exp; ++j) {
+    const ExpDev& e = ex[j];
+    double* out = xy + ((size_t)o * n_exp + pos_to_table[j]) * 2;
+    double x = __longlong_as_double(0x7ff8000000000000ll), y = x;
+    if (!w.failed) {
+      if (kepler_step(ph, w.oc, e.t - w.t_prev, w.r, w.v, w.rn, w.inv_r) < 0) {
+        w.failed = true;
+        atomicAdd(counters + 1, 1ull);
+      } else {
+        w.t_prev = e.t;
+        double rho[3];
+        apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
+        double px, py;
+        if (project(e, rho, px, py)) { x = px; y = py; }
+      }
+    }
+    out[0] = x;
+    out[1] = y;
+  }
+}
+
+template <int PT>
+cudaError_t launch_persistent_pt(const StackArgs& a, int n_sms, cudaStream_t st) {
+  // one wave: as many resident CTAs per SM as registers and shared memory allow
+#define NDT_CASE(TW, ET)                                                         \
+  if (a.orbit_tile == TW * 32 && a.exp_tile == ET) {                             \
+    int per_sm = 0;                                                              \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(               \
+        &per_sm, k_stack_persistent<PT, TW, ET>, kBlock, 0);                     \
+    if (e != cudaSuccess) return e;                                              \
+    const int blocks = n_sms * (per_sm > 0 ? per_sm : 1);                        \
+    k_stack_persistent<PT, TW, ET><<<blocks, kBlock, 0, st>>>(a);                \
+    return cudaGetLastError();                                                   \
+  }
+  NDT_CASE(1, 8) NDT_CASE(1, 16) NDT_CASE(1, 32)
+  NDT_CASE(2, 8) NDT_CASE(2, 16) NDT_CASE(2, 32)
+  NDT_CASE(4, 8) NDT_CASE(4, 16) NDT_CASE(4, 32)
+#undef NDT_CASE
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st) {
+  const int64_t blocks = (a.n + kBlock - 1) / kBlock;
+  if (blocks == 0) return cudaSuccess;
+  if (a.plane_type == kF32) k_stack_plain<kF32><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  else if (a.plane_type == kBF16) k_stack_plain<kBF16><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  else k_stack_plain<kF16><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st) {
+  if (a.plane_type == kF32) return launch_persistent_pt<kF32>(a, n_sms, st);
+  if (a.plane_type == kBF16) return launch_persistent_pt<kBF16>(a, n_sms, st);
+  return launch_persistent_pt<kF16>(a, n_sms, st);
+}
+
+cudaError_t launch_predict(const double* states, int64_t n, double t0, const ExpDev* ex,
+                           const int32_t* pos_to_table, int32_t n_exp, Phys ph, double* xy,
+                           unsigned long long* counters, cudaStream_t st) {
+  const int64_t blocks = (n + kBlock - 1) / kBlock;
+  if (blocks == 0) return cudaSuccess;
+  k_predict<<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, ex, pos_to_table, n_exp, ph, xy,
+                                                counters);
+  return cudaGetLastError();
+}
+
+}  // namespace ndt

@@ -1,0 +1,357 @@
+// ndt_internal.cuh -- device data layout and the per-sample device code of
+// the stacking path (propagate -> light time -> project -> gather), shared by
+// the stacking and position-prediction kernels of this library.
+//
+// Paper mapping (arXiv 2503.08854): sec. 3 "SearchImages" (two-body motion
+// about the Sun, WCS projection), "FilterGPUIntersections" (keep pixels inside
+// the image), "FindLocalSignal" (Gaussian-PSF matched filter, here a gather
+// from precomputed planes) and the constant-flux combination.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ndt {
+
+constexpr int kTile = 32;          // plane tile edge (pixels); tiles are 32 x 32
+constexpr int kTileShift = 5;
+constexpr int kMaxPsfRadius = 16;  // R = ceil(4 sigma) with sigma <= 4
+constexpr int kMaxKeplerIters = 40;
+
+// Per-exposure constants on the device, derived on the host from the
+// exposure table (152 bytes).
+struct ExpDev {
+  double t;          // epoch (days)
+  double obs[3];     // observer, heliocentric ecliptic (AU)
+  double p0[3];      // unit vector of the tangent point, ecliptic frame
+  double ax[3];      // x = crpix_x + (rho . ax) / (rho . p0)
+  double ay[3];      // y = crpix_y + (rho . ay) / (rho . p0)
+  double crpix[2];   // 0-based
+  int64_t plane_off; // first element of this exposure's plane
+  int32_t W, H;
+  int32_t tiles_x;   // ceil(W / 32)
+  float s_psi;       // dequantisation scale of psi (1 for FP32 planes)
+  float s_phi;       // dequantisation scale of phi
+  int32_t pad_;
+};
+static_assert(sizeof(ExpDev) == 152, "ExpDev layout");
+
+struct Phys {
+  double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
+  double sqrt_gm;
+  double inv_gm;
+  float inv_c;      // 1 / c (day/AU) for the light-time correction; 0: none
+  int32_t force_free;
+};
+
+// Plane storage type tags.
+enum PlaneType : int32_t { kF32 = 0, kBF16 = 1, kF16 = 2 };
+
+// Element offset of pixel (ix, iy) inside an exposure plane (tile-major).
+__host__ __device__ __forceinline__ int64_t tile_offset(int ix, int iy, int tiles_x) {
+  return ((int64_t)((iy >> kTileShift) * tiles_x + (ix >> kTileShift)) << (2 * kTileShift)) +
+         ((iy & (kTile - 1)) << kTileShift) + (ix & (kTile - 1));
+}
+
+// ---------------------------------------------------------------------------
+// Compensated FP32 accumulation (Neumaier's variant of Kahan summation).
+// ---------------------------------------------------------------------------
+struct CSum {
+  float s, c;
+  __device__ __forceinline__ void add(float x) {
+    float t = __fadd_rn(s, x);
+    float e = (fabsf(s) >= fabsf(x)) ? __fadd_rn(__fsub_rn(s, t), x) : __fadd_rn(__fsub_rn(x, t), s);
+    c = __fadd_rn(c, e);
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
+};
+
+// ---------------------------------------------------------------------------
+// Stumpff functions C(z) = sum (-z)^k/(2k+2)!, S(z) = sum (-z)^k/(2k+3)!.
+// Horner evaluation of the Maclaurin series, with the number of terms chosen
+// from |z| so that the truncation error stays below 1e-17; closed forms for
+// |z| >= 1.5 (Bate, Mueller & White 1971, sec. 4.3).
+// ---------------------------------------------------------------------------
+// (-1)^k / (2k+2)! and (-1)^k / (2k+3)!, k = 0..10
+__device__ __forceinline__ constexpr double stumpff_c_coef(int k) {
+  return k == 0 ? 1.0 / 2 : k == 1 ? -1.0 / 24 : k == 2 ? 1.0 / 720 : k == 3 ? -1.0 / 40320
+       : k == 4 ? 1.0 / 3628800 : k == 5 ? -1.0 / 479001600 : k == 6 ? 1.0 / 87178291200.0
+       : k == 7 ? -1.0 / 20922789888000.0 : k == 8 ? 1.0 / 6402373705728000.0
+       : k == 9 ? -1.0 / 2432902008176640000.0 : 1.0 / 1124000727777607680000.0;
+}
+__device__ __forceinline__ constexpr double stumpff_s_coef(int k) {
+  return k == 0 ? 1.0 / 6 : k == 1 ? -1.0 / 120 : k == 2 ? 1.0 / 5040 : k == 3 ? -1.0 / 362880
+       : k == 4 ? 1.0 / 39916800 : k == 5 ? -1.0 / 6227020800.0 : k == 6 ? 1.0 / 1307674368000.0
+       : k == 7 ? -1.0 / 355687428096000.0 : k == 8 ? 1.0 / 121645100408832000.0
+       : k == 9 ? -1.0 / 51090942171709440000.0 : 1.0 / 25852016738884976640000.0;
+}
+
+template <int M>
+__device__ __forceinline__ void stumpff_series(double z, double& C, double& S) {
+  double c = stumpff_c_coef(M - 1), s = stumpff_s_coef(M - 1);
+#pragma unroll
+  for (int k = M - 2; k >= 0; --k) {
+    c = fma(c, z, stumpff_c_coef(k));
+    s = fma(s, z, stumpff_s_coef(k));
+  }
+  C = c;
+  S = s;
+}
+
+__device__ __forceinline__ void stumpff(double z, double& C, double& S) {
+  const double az = fabs(z);
+  if (az < 1e-3) {
+    stumpff_series<4>(z, C, S);
+  } else if (az < 0.05) {
+    stumpff_series<6>(z, C, S);
+  } else if (az < 0.3) {
+    stumpff_series<8>(z, C, S);
+  } else if (az < 1.5) {
+    stumpff_series<11>(z, C, S);
+  } else if (z > 0.0) {
+    double q = sqrt(z), sn, cs;
+    sincos(q, &sn, &cs);
+    C = (1.0 - cs) / z;
+    S = (q - sn) / (z * q);
+  } else {
+    double q = sqrt(-z);
+    double e = exp(q), ei = 1.0 / e;
+    double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
+    C = (ch - 1.0) / (-z);
+    S = (sh - q) / ((-z) * q);
+  }
+}
+
+// Per-orbit constants of the two-body motion.
+struct OrbitConst {
+  double alpha;        // 2/r - v^2/GM (reciprocal semi-major axis), conserved
+  double period;       // orbital period (bound orbits), else 0
+  double inv_period;
+};
+
+__device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
+                                                  const double v[3], double inv_r) {
+  OrbitConst oc;
+  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  oc.alpha = 2.0 * inv_r - v2 * ph.inv_gm;
+  if (oc.alpha > 0.0) {
+    double n = ph.sqrt_gm * oc.alpha * sqrt(oc.alpha);   // mean motion
+    oc.period = 6.283185307179586476925 / n;
+    oc.inv_period = n / 6.283185307179586476925;
+  } else {
+    oc.period = 0.0;
+    oc.inv_period = 0.0;
+  }
+  return oc;
+}
+
+// ---------------------------------------------------------------------------
+// One two-body step of length dt (universal-variable formulation), updating
+// the state (r, v) in place together with |r| and 1/|r|.
+//
+// The universal Kepler equation F(chi) = 0 (F as in Bate, Mueller & White,
+// eq. 4.4-14) is solved by the Laguerre-Conway iteration (Conway 1986) from a
+// third-order series guess in dt.  F, F' and F'' are evaluated in FP64; only
+// the correction ratio is formed in FP32, so every iterate is an FP64 value
+// and the converged root satisfies F = 0 to FP64 rounding.  The iteration
+// stops once the correction is below 1e-9; the Lagrange coefficients are then
+// corrected to first order in that last step instead of re-evaluating the
+// Stumpff functions (the second-order remainder is below 1e-17).
+// Returns the number of evaluations, or -1 when kMaxKeplerIters is reached.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc, double dt,
+                                           double r[3], double v[3], double& rn, double& inv_r) {
+  if (ph.force_free) {
+    for (int i = 0; i < 3; ++i) r[i] = fma(v[i], dt, r[i]);
+    rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    inv_r = 1.0 / rn;
+    return 0;
+  }
+  if (oc.alpha > 0.0) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
+  const double alpha = oc.alpha;
+  const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) / ph.sqrt_gm;
+  const double a1 = fma(-alpha, rn, 1.0);            // 1 - alpha r0
+  const double sdt = ph.sqrt_gm * dt;
+  // third-order series of chi(dt): u - sig0 u^2/(2 r0) - u^3/6 (1/r0 - alpha - 3 sig0^2/r0^2)
+  const double u = sdt * inv_r;
+  double chi = u - 0.5 * sig0 * inv_r * u * u -
+               (u * u * u / 6.0) * (inv_r - alpha - 3.0 * sig0 * sig0 * inv_r * inv_r);
+  if (fabs(alpha) * chi * chi > 0.25 || !(fabs(chi) < 1e30)) {
+    chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
+  }
+  int it;
+  for (it = 1; it <= kMaxKeplerIters; ++it) {
+    const double chi2 = chi * chi;
+    const double z = alpha * chi2;
+    double C, S;
+    stumpff(z, C, S);
+    const double chi2C = chi2 * C;
+    const double chi3S = chi2 * chi * S;
+    const double chi1mzS = chi * fma(-z, S, 1.0);
+    const double F = fma(sig0, chi2C, fma(a1, chi3S, fma(rn, chi, -sdt)));
+    const double dF = fma(sig0, chi1mzS, fma(a1, chi2C, rn));        // = |r|
+    const double d2F = fma(sig0, fma(-z, C, 1.0), a1 * chi1mzS);
+    const float Ff = (float)F, dFf = (float)dF, d2Ff = (float)d2F;
+    const float disc = fabsf(16.0f * dFf * dFf - 20.0f * Ff * d2Ff);
+    const float delta = 5.0f * Ff / (dFf + sqrtf(disc));
+    if (fabsf(delta) <= 1e-9f) {
+      // outputs at chi - delta, to first order in delta
+      const double d = (double)delta;
+      const double chi2C_c = fma(-d, chi1mzS, chi2C);
+      const double f = 1.0 - chi2C_c * inv_r;
+      const double g = dt - fma(-d, chi2C, chi3S) / ph.sqrt_gm;
+      const double rc = fma(-d, d2F, dF);
+      const double inv_rc = 1.0 / rc;
+      const double fdot = -ph.sqrt_gm * fma(-d, fma(-z, C, 1.0), chi1mzS) * inv_rc * inv_r;
+      const double gdot = 1.0 - chi2C_c * inv_rc;
+      double rr[3];
+      for (int i = 0; i < 3; ++i) rr[i] = fma(f, r[i], g * v[i]);
+      for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], gdot * v[i]);
+      for (int i = 0; i < 3; ++i) r[i] = rr[i];
+      rn = rc;
+      inv_r = inv_rc;
+      return it;
+    }
+    chi -= (double)delta;
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Light-time corrected topocentric vector.  With (r, v) the geometric state
+// at the exposure epoch, the emitted position is expanded to second order in
+// the light time tau: r(t - tau) = r - tau v - (tau^2 / 2) GM r / |r|^3 (the
+// third-order term is below 1e-11 AU for every orbit class in the
+// workloads).  tau is found by one fixed-point refinement of tau = |rho| / c
+// starting from the geometric distance; tau only needs ~1e-7 relative
+// accuracy, so its square roots are FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], const double v[3],
+                                             double inv_r, const double obs[3], double rho[3]) {
+  double d[3] = {r[0] - obs[0], r[1] - obs[1], r[2] - obs[2]};
+  if (ph.inv_c == 0.0f) {
+    rho[0] = d[0]; rho[1] = d[1]; rho[2] = d[2];
+    return;
+  }
+  const double kacc = ph.force_free ? 0.0 : -0.5 * ph.gm * inv_r * inv_r * inv_r;
+  float tau = __fsqrt_rn((float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * ph.inv_c;
+  for (int pass = 0; pass < 2; ++pass) {
+    const double t = (double)tau;
+    const double h = kacc * t * t;   // -(tau^2/2) GM / |r|^3
+    for (int i = 0; i < 3; ++i) rho[i] = fma(h, r[i], fma(-t, v[i], d[i]));
+    if (pass == 0)
+      tau = __fsqrt_rn((float)(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2])) * ph.inv_c;
+  }
+}
+
+// TAN projection through the precomputed per-exposure rows (Calabretta &
+// Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
+// Returns false when cos c <= 0.
+__device__ __forceinline__ bool project(const ExpDev& e, const double rho[3], double& x, double& y) {
+  const double den = rho[0] * e.p0[0] + rho[1] * e.p0[1] + rho[2] * e.p0[2];
+  if (!(den > 0.0)) return false;
+  const double inv = 1.0 / den;
+  x = fma(rho[0] * e.ax[0] + rho[1] * e.ax[1] + rho[2] * e.ax[2], inv, e.crpix[0]);
+  y = fma(rho[0] * e.ay[0] + rho[1] * e.ay[1] + rho[2] * e.ay[2], inv, e.crpix[1]);
+  return true;
+}
+
+// Nearest pixel (pixel i spans [i - 1/2, i + 1/2)); false outside the image.
+__device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double x, double y, int& ix, int& iy) {
+  const double fx = floor(x + 0.5), fy = floor(y + 0.5);
+  if (!(fx >= 0.0 && fx < (double)e.W && fy >= 0.0 && fy < (double)e.H)) return false;
+  ix = (int)fx;
+  iy = (int)fy;
+  return true;
+}
+
+template <int PT>
+__device__ __forceinline__ float2 gather_plane(const void* __restrict__ planes, const ExpDev& e,
+                                               int ix, int iy) {
+  const int64_t off = e.plane_off + tile_offset(ix, iy, e.tiles_x);
+  if (PT == kF32) {
+    return __ldg(reinterpret_cast<const float2*>(planes) + off);
+  } else if (PT == kBF16) {
+    __nv_bfloat162 q = __ldg(reinterpret_cast<const __nv_bfloat162*>(planes) + off);
+    float2 f = __bfloat1622float2(q);
+    return make_float2(f.x * e.s_psi, f.y * e.s_phi);
+  } else {
+    __half2 q = __ldg(reinterpret_cast<const __half2*>(planes) + off);
+    float2 f = __half22float2(q);
+    return make_float2(f.x * e.s_psi, f.y * e.s_phi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the kernel translation units).
+// ---------------------------------------------------------------------------
+struct PlaneJob {
+  const float* image;   // row-major H x W
+  const float* var;     // row-major H x W, or null (constant variance)
+  float var_c;
+  float sigma;
+  int32_t W, H, tiles_x, tiles_y;
+  int64_t plane_off;    // element offset in the FP32 plane buffer
+};
+
+cudaError_t launch_planes_f32(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, float2* out,
+                              cudaStream_t st);
+cudaError_t launch_plane_absmax(const PlaneJob* jobs_dev, int n_jobs, const float2* planes,
+                                unsigned int* absmax2, cudaStream_t st);
+cudaError_t launch_plane_quantize(const PlaneJob* jobs_dev, int n_jobs, const float2* planes,
+                                  const unsigned int* absmax2, int plane_type, void* out,
+                                  float* scales2, cudaStream_t st);
+cudaError_t launch_plane_decode(const void* planes, int plane_type, const ExpDev* e_host_copy,
+                                float* psi, float* phi, cudaStream_t st);
+
+struct StackArgs {
+  const double* states;        // SoA 6 x n
+  int64_t n;
+  double t0;
+  const ExpDev* ex;            // sorted by epoch
+  int32_t n_exp;
+  const void* planes;
+  int32_t plane_type;
+  // families (CSR over sorted exposure positions); n_fam = 0: all x all
+  int32_t n_fam;
+  const int64_t* fam_orb_off;
+  const int64_t* fam_exp_off;
+  const int32_t* fam_exp_pos;
+  // persistent queue
+  const int64_t* item_off;     // n_fam + 1 prefix of items per family (queue order)
+  const int32_t* fam_order;    // queue order -> family
+  int64_t n_items;
+  unsigned long long* queue_head;
+  int32_t orbit_tile, exp_tile;
+  // outputs (per orbit, any may be null except snr)
+  float* psi_sum;
+  float* phi_sum;
+  int32_t* nobs;
+  float* snr;
+  int32_t min_obs;
+  unsigned long long* counters;  // [0] valid samples, [1] Kepler failures
+  Phys ph;
+};
+
+cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);
+cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st);
+cudaError_t launch_predict(const double* states, int64_t n, double t0, const ExpDev* ex,
+                           const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph,
+                           double* xy, unsigned long long* counters, cudaStream_t st);
+
+// top-k
+struct TopkScratch {
+  unsigned int* hist;          // 256 bins
+  unsigned int* sel_state;     // [prefix, k_remaining, n_less, mask]
+  unsigned int* block_counts;  // 2 * max_blocks
+  unsigned long long* items;   // k composite keys (key32 << 32 | idx32)
+  int max_blocks;
+};
+size_t topk_scratch_bytes(int64_t n, int64_t k);
+cudaError_t launch_topk(const float* snr, int64_t n, int64_t k, void* scratch, size_t scratch_bytes,
+                        int64_t* idx_out, float* snr_out, int* launches, cudaStream_t st);
+
+}  // namespace ndt

@@ -1,0 +1,211 @@
+"""ctypes binding of the C ABI in ``include/ndt.h`` (argument marshalling only).
+
+Every function has the name of its C entry point without the ``ndt_``
+prefix and forwards raw pointers: torch tensors (CUDA or CPU) and numpy
+arrays are accepted and passed as device or host addresses; the library
+decides whether to copy.  All computation runs in ``libndt.so``; there is no
+fallback: if the library is missing this module raises on import.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libndt.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; "
+                      f"g.build()'` (needs nvcc) before using the CUDA path")
+
+_lib = C.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, ENOCONV = range(7)
+PLANE_F32, PLANE_BF16, PLANE_F16 = 0, 1, 2
+LAUNCH_PLAIN, LAUNCH_PERSISTENT = 0, 1
+_PLANE_NAMES = {"f32": PLANE_F32, "bf16": PLANE_BF16, "f16": PLANE_F16}
+
+
+class Exposure(C.Structure):
+    _fields_ = [("mjd", C.c_double), ("obs_xyz", C.c_double * 3), ("crval", C.c_double * 2),
+                ("crpix", C.c_double * 2), ("cd", C.c_double * 4), ("psf_sigma_px", C.c_float),
+                ("variance", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("samples", C.c_int64),
+                ("valid_samples", C.c_int64), ("kepler_failures", C.c_int64),
+                ("last_stack_ms", C.c_float), ("last_planes_ms", C.c_float),
+                ("last_topk_ms", C.c_float), ("orbit_tile", C.c_int32), ("exp_tile", C.c_int32),
+                ("launch_mode", C.c_int32), ("plane_dtype", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+assert C.sizeof(Exposure) == 112
+
+_vp, _i32, _i64, _f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_lib.ndt_create.argtypes = [C.POINTER(_vp), C.c_int, _vp]
+_lib.ndt_destroy.argtypes = [_vp]
+_lib.ndt_destroy.restype = None
+_lib.ndt_last_error.argtypes = [_vp]
+_lib.ndt_last_error.restype = C.c_char_p
+_lib.ndt_set_constants.argtypes = [_vp, _f64, _f64, _f64]
+_lib.ndt_load_exposures.argtypes = [_vp, C.POINTER(Exposure), _i32, C.POINTER(_vp), C.POINTER(_vp), _i32]
+_lib.ndt_stack_orbits.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp]
+_lib.ndt_topk_candidates.argtypes = [_vp, _i64, _vp, _vp, C.POINTER(_i64)]
+_lib.ndt_predict_positions.argtypes = [_vp, _vp, _f64, _i64, _vp]
+_lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
+_lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
+_lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
+_lib.ndt_get_stats.argtypes = [_vp, C.POINTER(Stats)]
+_lib.ndt_synchronize.argtypes = [_vp]
+
+
+class NdtError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"ndt status {status}: {message}")
+        self.status = status
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor arguments must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array arguments must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(ctx, status):
+    if status != OK:
+        raise NdtError(status, _lib.ndt_last_error(ctx).decode())
+
+
+def create(device=0, stream=None):
+    """ndt_create.  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    h = _vp()
+    raw = getattr(stream, "cuda_stream", stream)
+    st = _lib.ndt_create(C.byref(h), int(device), raw)
+    if st != OK:
+        raise NdtError(st, _lib.ndt_last_error(None).decode())
+    return h
+
+
+def destroy(ctx):
+    _lib.ndt_destroy(ctx)
+
+
+def last_error(ctx):
+    return _lib.ndt_last_error(ctx).decode()
+
+
+def set_constants(ctx, gm, c_light, obliquity_rad):
+    _check(ctx, _lib.ndt_set_constants(ctx, gm, c_light, obliquity_rad))
+
+
+def exposure_table(ex):
+    """Marshal a ``synth.Exposures`` table into an array of ndt_exposure."""
+    n = len(ex.mjd)
+    arr = (Exposure * n)()
+    cd = np.asarray(ex.cd, dtype=np.float64).reshape(n, 4)
+    for j in range(n):
+        e = arr[j]
+        e.mjd = float(ex.mjd[j])
+        e.obs_xyz[:] = [float(v) for v in ex.obs[j]]
+        e.crval[:] = [float(v) for v in ex.crval[j]]
+        e.crpix[:] = [float(v) for v in ex.crpix[j]]
+        e.cd[:] = [float(v) for v in cd[j]]
+        e.psf_sigma_px = float(ex.sigma[j])
+        e.variance = float(ex.var[j])
+        e.width = int(ex.width[j])
+        e.height = int(ex.height[j])
+    return arr
+
+
+def load_exposures(ctx, ex, images, variances=None, plane_dtype="f32"):
+    """``images``: a sequence of per-exposure buffers or one (n, H, W) buffer."""
+    table = exposure_table(ex)
+    n = len(table)
+    if hasattr(images, "shape") and len(images.shape) == 3:
+        images = [images[j] for j in range(n)]
+    ptrs = (_vp * n)(*[_ptr(im) for im in images])
+    vptrs = None
+    if variances is not None:
+        if hasattr(variances, "shape") and len(variances.shape) == 3:
+            variances = [variances[j] for j in range(n)]
+        vptrs = (_vp * n)(*[_ptr(v) for v in variances])
+    dt = _PLANE_NAMES.get(plane_dtype, plane_dtype)
+    _check(ctx, _lib.ndt_load_exposures(ctx, table, n, ptrs, vptrs, int(dt)))
+
+
+def stack_orbits(ctx, states_soa, t0, n_orbits, families=None, min_obs=1, psi_sum=None,
+                 phi_sum=None, nobs=None, snr=None):
+    """``states_soa``: 6 x n_orbits FP64 buffer (x, y, z, vx, vy, vz rows).
+    ``families``: (fam_orbit_off int64, fam_exp_off int64, fam_exp_idx int32) or None."""
+    if families is None:
+        fo = fe = fi = None
+        nf = 0
+    else:
+        fo, fe, fi = families
+        nf = len(fo) - 1
+    _check(ctx, _lib.ndt_stack_orbits(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(fo),
+                                      _ptr(fe), _ptr(fi), nf, int(min_obs), _ptr(psi_sum),
+                                      _ptr(phi_sum), _ptr(nobs), _ptr(snr)))
+
+
+def topk_candidates(ctx, k, idx_out=None, snr_out=None):
+    got = _i64(0)
+    _check(ctx, _lib.ndt_topk_candidates(ctx, int(k), _ptr(idx_out), _ptr(snr_out), C.byref(got)))
+    return got.value
+
+
+def predict_positions(ctx, states_soa, t0, n_orbits, xy_out):
+    _check(ctx, _lib.ndt_predict_positions(ctx, _ptr(states_soa), float(t0), int(n_orbits),
+                                           _ptr(xy_out)))
+
+
+def get_planes(ctx, j, psi_out=None, phi_out=None):
+    _check(ctx, _lib.ndt_get_planes(ctx, int(j), _ptr(psi_out), _ptr(phi_out)))
+
+
+def set_launch(ctx, mode, orbit_tile=64, exp_tile=16, use_graph=False):
+    _check(ctx, _lib.ndt_set_launch(ctx, int(mode), int(orbit_tile), int(exp_tile), int(bool(use_graph))))
+
+
+def autotune(ctx, states_soa, t0, n_orbits, families=None, times_ms=None):
+    if families is None:
+        fo = fe = fi = None
+        nf = 0
+    else:
+        fo, fe, fi = families
+        nf = len(fo) - 1
+    _check(ctx, _lib.ndt_autotune(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(fo),
+                                  _ptr(fe), _ptr(fi), nf, _ptr(times_ms)))
+
+
+def get_stats(ctx):
+    s = Stats()
+    _check(ctx, _lib.ndt_get_stats(ctx, C.byref(s)))
+    return s.as_dict()
+
+
+def synchronize(ctx):
+    _check(ctx, _lib.ndt_synchronize(ctx))
+
+
+def exported_symbols():
+    """Names of the C entry points this binding uses (all must be exported)."""
+    return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
+            "ndt_load_exposures", "ndt_stack_orbits", "ndt_topk_candidates",
+            "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_autotune",
+            "ndt_get_stats", "ndt_synchronize"]

@@ -193,3 +193,135 @@ def noise_images(ex: Exposures, seed: int, dtype=np.float32):
         out[j] = rng.standard_normal((int(ex.height[j]), int(ex.width[j])), dtype=np.float32) \
             * np.float32(math.sqrt(ex.var[j]))
     return out
+
+
+# --------------------------------------------------------------------------
+# MBA-scale survey (dense coverage, irregular cadence)
+# --------------------------------------------------------------------------
+
+def state_from_elements(a, e, inc, node, argp, true_anom, gm=GAUSS_K ** 2):
+    """Heliocentric ecliptic state from classical elements with the TRUE anomaly
+    (the perifocal conic formula; orbit sampling, no time propagation)."""
+    a, e, inc, node, argp, nu = (np.asarray(x, dtype=np.float64) for x in
+                                 (a, e, inc, node, argp, true_anom))
+    p = a * (1.0 - e * e)
+    r = p / (1.0 + e * np.cos(nu))
+    pf = np.stack([r * np.cos(nu), r * np.sin(nu), np.zeros_like(nu)], -1)
+    vf = np.sqrt(gm / p)[..., None] * np.stack([-np.sin(nu), e + np.cos(nu), np.zeros_like(nu)], -1)
+    cO, sO, ci, si, cw, sw = np.cos(node), np.sin(node), np.cos(inc), np.sin(inc), np.cos(argp), np.sin(argp)
+    R = np.stack([np.stack([cO * cw - sO * sw * ci, -cO * sw - sO * cw * ci, sO * si], -1),
+                  np.stack([sO * cw + cO * sw * ci, -sO * sw + cO * cw * ci, -cO * si], -1),
+                  np.stack([sw * si, cw * si, ci], -1)], -2)
+    pos = np.einsum("...ij,...j->...i", R, pf)
+    vel = np.einsum("...ij,...j->...i", R, vf)
+    return np.concatenate([pos, vel], -1)
+
+
+def irregular_cadence(rng, n_exp, nights, mjd_start, visits=(1, 4), gap_min=15.0, snap_s=90.0):
+    """Survey cadence: each night has U{visits} visits at least ``gap_min``
+    minutes apart inside a 6 h window; the n_exp exposures are spread over the
+    visits as evenly as possible, ``snap_s`` seconds apart within a visit."""
+    times = []
+    for night in range(int(nights)):
+        k = int(rng.integers(visits[0], visits[1] + 1))
+        while True:
+            t = np.sort(rng.uniform(0.0, 0.25, k))
+            if k == 1 or np.min(np.diff(t)) >= gap_min / 1440.0:
+                break
+        times.extend(mjd_start + night + 0.1 + t)
+    times = np.asarray(times)
+    per = np.full(len(times), n_exp // len(times))
+    per[: n_exp - per.sum()] += 1
+    mjd = np.concatenate([t + np.arange(m) * snap_s / 86400.0 for t, m in zip(times, per)])
+    return np.sort(mjd)[:n_exp]
+
+
+def mba_sky(*, n_exp=200, nights=30, size=4096, n_true=1000, fam_size=16384, seed=2,
+            mjd_start=60100.0, lon=2.0, lon_half=0.055, scale_arcsec=10.5,
+            snr_range=(0.5, 3.0), jitter_r=3e-4, jitter_v=1e-5) -> Sky:
+    """MBA-scale workload.  1000 main-belt asteroids (a in [2.1, 3.3] AU,
+    e < 0.2, i < 20 deg) near opposition at the mid-span epoch t0, each the
+    seed of a family of ``fam_size`` candidate orbits (the true state plus
+    seeded state jitter), 16.4 M candidates in all.  Exposures follow an
+    irregular 1-4 visit/night cadence over ``nights`` nights; pointings track
+    a circular reference body at 2.7 AU; each exposure's chip is offset so
+    that it covers a random 60-100 % of the population's extent; PSF sigma
+    ~ U(1.2, 2.0) px and variance log-uniform in [0.5, 2] per exposure.
+    Candidate orbit o of family f is index f * fam_size + (o % fam_size);
+    member 0 of every family is the true state."""
+    rng = np.random.default_rng(seed)
+    mjd = irregular_cadence(rng, n_exp, nights, mjd_start)
+    t0 = float(mjd_start + nights / 2.0)
+    obs = observer_position(mjd, t0, lon)
+    crval = tracking_pointings(mjd, obs, t0, 2.7, lon)
+    s = scale_arcsec / 3600.0
+    # population extent along x in pixels (geocentric longitude spread near opposition)
+    span_px = 2.0 * math.degrees(lon_half) * 1.9 / s
+    cover = rng.uniform(0.6, 1.0, n_exp)
+    shift = (1.0 - cover) * span_px * rng.choice([-1.0, 1.0], n_exp)
+    crpix = np.stack([size / 2.0 + shift, np.full(n_exp, size / 2.0)], -1)
+    sigma = rng.uniform(1.2, 2.0, n_exp).astype(np.float32).astype(np.float64)
+    var = np.exp(rng.uniform(math.log(0.5), math.log(2.0), n_exp)).astype(np.float32).astype(np.float64)
+    ex = Exposures(mjd=mjd, obs=obs, crval=crval, crpix=crpix,
+                   cd=np.tile(np.array([[-s, 0.0], [0.0, s]]), (n_exp, 1, 1)), sigma=sigma, var=var,
+                   width=np.full(n_exp, size, np.int32), height=np.full(n_exp, size, np.int32))
+    a = rng.uniform(2.1, 3.3, n_true)
+    e = rng.uniform(0.0, 0.2, n_true)
+    inc = np.radians(rng.uniform(0.0, 20.0, n_true))
+    u = rng.uniform(-0.05, 0.05, n_true)                  # argument of latitude: near a node
+    u = np.where(rng.random(n_true) < 0.5, u, u + math.pi)
+    lam = lon + rng.uniform(-lon_half, lon_half, n_true)  # heliocentric longitude at t0
+    node = lam - np.arctan2(np.cos(inc) * np.sin(u), np.cos(u))
+    argp = rng.uniform(0.0, 2 * math.pi, n_true)
+    true_states = state_from_elements(a, e, inc, node, argp, u - argp)
+    states = np.repeat(true_states, fam_size, axis=0)
+    jit = np.concatenate([rng.normal(0.0, jitter_r, (len(states), 3)),
+                          rng.normal(0.0, jitter_v, (len(states), 3))], 1)
+    jit[::fam_size] = 0.0
+    states += jit
+    snr = rng.uniform(*snr_range, n_true)
+    flux = flux_for_snr(snr, 1.6, 1.0)
+    return Sky(name="mba", ex=ex, t0=t0, states=states, inj_states=true_states, inj_flux=flux,
+               inj_orbit=np.arange(n_true, dtype=np.int64) * fam_size, seed=seed,
+               meta=dict(fam_size=fam_size, n_true=n_true, cover=cover, inj_snr=snr, size=size))
+
+
+def noise_images_torch(ex: Exposures, seed: int, device):
+    """N(0, var_j) noise images drawn on a torch device (seeded generator)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) + 1000003)
+    out = torch.empty((ex.n, int(ex.height[0]), int(ex.width[0])), dtype=torch.float32, device=device)
+    for j in range(ex.n):
+        out[j].normal_(0.0, math.sqrt(float(ex.var[j])), generator=g)
+    return out
+
+
+def render_sources_torch(images, xy, flux, sigma, radius=6.0):
+    """``render_sources`` for a torch image stack: xy (n_src, n_exp, 2) tensor."""
+    import torch
+    n_exp, H, W = images.shape
+    dev = images.device
+    rad = int(math.ceil(radius * float(np.max(sigma))))
+    off = torch.arange(-rad, rad + 2, device=dev, dtype=torch.float64)
+    xy = torch.as_tensor(xy, device=dev, dtype=torch.float64)
+    flux = torch.as_tensor(np.asarray(flux), device=dev, dtype=torch.float64)
+    sg = torch.as_tensor(np.asarray(sigma), device=dev, dtype=torch.float64)
+    for j in range(n_exp):
+        p = xy[:, j]
+        ok = torch.isfinite(p).all(-1)
+        if not bool(ok.any()):
+            continue
+        p, f = p[ok], flux[ok]
+        bx = torch.floor(p[:, 0])[:, None] + off[None, :]      # (m, K)
+        by = torch.floor(p[:, 1])[:, None] + off[None, :]
+        s2 = sg[j] ** 2
+        gx = torch.exp(-0.5 * (bx - p[:, :1]) ** 2 / s2)
+        gy = torch.exp(-0.5 * (by - p[:, 1:]) ** 2 / s2)
+        val = (f / (2 * math.pi * s2))[:, None, None] * gy[:, :, None] * gx[:, None, :]
+        X = bx[:, None, :].expand_as(val)
+        Y = by[:, :, None].expand_as(val)
+        m = (X >= 0) & (X < W) & (Y >= 0) & (Y < H)
+        lin = (Y[m] * W + X[m]).long()
+        images[j].view(-1).index_add_(0, lin, val[m].to(images.dtype))
+    return images

@@ -1,0 +1,341 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle, through the C ABI.
+
+Cases span several 32 x 32 plane tiles with ragged tails, the full plain-method
+tiny workload (65,536 orbits x 10 exposures of 512 x 512), both launch forms,
+orbit families, host and device pointers, reduced-precision planes, force-free
+motion and the degenerate inputs of the method."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_08854_gb300 import ndt, synth
+
+from _gpu_helpers import Gpu, POS_TOL, check_stack, check_topk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+def _ragged_sky(seed=3, n_exp=6, size=100):
+    sky = synth.grid_sky(n_exp=n_exp, size=size, n_r=4, n_v=32, scale_arcsec=1.0, inj_snr=4.0,
+                         n_inj=3, seed=seed)
+    # per-exposure PSF widths and variances (FP32-representable)
+    rng = np.random.default_rng(seed)
+    sky.ex.sigma = rng.uniform(1.0, 2.2, n_exp).astype(np.float32).astype(np.float64)
+    sky.ex.var = rng.uniform(0.5, 2.0, n_exp).astype(np.float32).astype(np.float64)
+    return sky
+
+
+def _images(sky, inject=True):
+    imgs = synth.noise_images(sky.ex, sky.seed)
+    if inject:
+        xy = O.predict(sky.inj_states, sky.t0, sky.ex)
+        synth.render_sources(imgs, xy, sky.inj_flux, sky.ex.sigma)
+    return imgs
+
+
+# ---------------------------------------------------------------- planes ----
+
+@pytest.mark.parametrize("per_pixel_var", [False, True])
+def test_planes_match_oracle(gpu, per_pixel_var):
+    rng = np.random.default_rng(1)
+    sky = _ragged_sky()
+    ex = sky.ex.subset([0, 1, 2])
+    ex.width = np.array([100, 37, 70], np.int32)
+    ex.height = np.array([70, 65, 33], np.int32)
+    imgs = [rng.normal(size=(ex.height[j], ex.width[j])).astype(np.float32) for j in range(3)]
+    var = [rng.uniform(0.5, 2.0, size=im.shape).astype(np.float32) for im in imgs] \
+        if per_pixel_var else None
+    d = [torch.from_numpy(im).to(gpu.dev) for im in imgs]
+    dv = None if var is None else [torch.from_numpy(v).to(gpu.dev) for v in var]
+    torch.cuda.synchronize()
+    ndt.load_exposures(gpu.ctx, ex, d, variances=dv)
+    for j in range(3):
+        psi, phi = gpu.planes(j, ex.height[j], ex.width[j])
+        rp, rf = O.planes(imgs[j], ex.sigma[j], var[j] if var is not None else ex.var[j])
+        np.testing.assert_allclose(psi, rp, rtol=1e-5, atol=2e-6 * np.abs(rp).max())
+        np.testing.assert_allclose(phi, rf, rtol=1e-5, atol=1e-7 * np.abs(rf).max())
+
+
+@pytest.mark.parametrize("plane", ["bf16", "f16"])
+def test_reduced_precision_planes_error_bound(gpu, plane):
+    """RNE of value/scale: |error| <= half an ulp of the stored format (2^-9
+    relative for BF16, 2^-12 for FP16 normals) plus the FP32 plane error."""
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs, plane=plane)
+    rel = 2.0 ** -8 if plane == "bf16" else 2.0 ** -11
+    for j in range(sky.ex.n):
+        psi, phi = gpu.planes(j, 100, 100)
+        rp, rf = O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j])
+        s = np.abs(rp).max() / 16384
+        assert np.all(np.abs(psi - rp) <= rel * np.abs(rp) + s * 2.0 ** -14 + 2e-6 * np.abs(rp).max())
+        assert np.all(np.abs(phi - rf) <= rel * np.abs(rf) + 1e-7 * rf.max())
+
+
+# ------------------------------------------------------------- positions ----
+
+def test_positions_match_oracle_plain_workload(gpu):
+    sky = synth.grid_sky()
+    imgs = np.zeros((sky.ex.n, 512, 512), np.float32)
+    gpu.load(sky.ex, imgs)
+    sel = np.random.default_rng(0).choice(len(sky.states), 4096, replace=False)
+    st = sky.states[sel]
+    xy = gpu.predict(st, sky.t0, sky.ex.n)
+    ref = O.predict(st, sky.t0, sky.ex, nthreads=0)
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(xy))
+    err = np.abs(xy[fin] - ref[fin]).max()
+    assert err <= POS_TOL, f"max position error {err:.3g} px"
+
+
+def _mixed_population(rng, n):
+    """NEO-like (q < 1.3 AU, e up to 0.8), main belt, Kuiper belt (30-50 AU) and
+    hyperbolic states at random orientations."""
+    mu = O.gm_sun()
+    out = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:
+            a, e = rng.uniform(0.8, 2.5), rng.uniform(0.3, 0.8)
+        elif kind == 1:
+            a, e = rng.uniform(2.1, 3.3), rng.uniform(0.0, 0.2)
+        elif kind == 2:
+            a, e = rng.uniform(30.0, 50.0), rng.uniform(0.0, 0.2)
+        else:
+            a, e = -rng.uniform(1.0, 5.0), rng.uniform(1.1, 2.0)
+        nu = rng.uniform(-2.0, 2.0) if kind == 3 else rng.uniform(0, 2 * math.pi)
+        p = a * (1 - e * e)
+        r = p / (1 + e * math.cos(nu))
+        pos = np.array([r * math.cos(nu), r * math.sin(nu), 0.0])
+        vel = math.sqrt(mu / p) * np.array([-math.sin(nu), e + math.cos(nu), 0.0])
+        inc, node, argp = rng.uniform(0, 0.5), rng.uniform(0, 2 * math.pi), rng.uniform(0, 2 * math.pi)
+        def rot(v):
+            c, s = math.cos(argp), math.sin(argp)
+            v = np.array([c * v[0] - s * v[1], s * v[0] + c * v[1], v[2]])
+            c, s = math.cos(inc), math.sin(inc)
+            v = np.array([v[0], c * v[1] - s * v[2], s * v[1] + c * v[2]])
+            c, s = math.cos(node), math.sin(node)
+            return np.array([c * v[0] - s * v[1], s * v[0] + c * v[1], v[2]])
+        out.append(np.concatenate([rot(pos), rot(vel)]))
+    return np.array(out)
+
+
+def test_positions_mixed_orbit_classes_long_span(gpu):
+    """NEO, main-belt, Kuiper-belt and hyperbolic orbits over a year: each
+    exposure points at one object, so every object is near the centre of
+    several exposures; all finite positions within 1e4 px are compared."""
+    rng = np.random.default_rng(7)
+    n_obj, n_exp = 24, 48
+    states = _mixed_population(rng, n_obj)
+    t0 = 60200.0
+    mjd = np.sort(t0 + rng.uniform(-180, 180, n_exp))
+    obs = synth.observer_position(mjd, t0, 0.3)
+    crval = np.zeros((n_exp, 2))
+    for j in range(n_exp):
+        rho, _ = O.apparent(states[j % n_obj], t0, mjd[j], obs[j])
+        _, _, _, ra, dec = O.project(rho, [0, 0], [0, 0], [[1, 0], [0, 1]])
+        crval[j] = [math.degrees(ra) + rng.normal() * 1e-3, math.degrees(dec) + rng.normal() * 1e-3]
+    s = 1.0 / 3600
+    ex = synth.Exposures(mjd=mjd, obs=obs, crval=crval, crpix=np.tile([1024.0, 1024.0], (n_exp, 1)),
+                         cd=np.tile([[-s, 0], [0, s]], (n_exp, 1, 1)), sigma=np.full(n_exp, 1.5),
+                         var=np.ones(n_exp), width=np.full(n_exp, 64, np.int32),
+                         height=np.full(n_exp, 64, np.int32))
+    gpu.load(ex, np.zeros((n_exp, 64, 64), np.float32))
+    xy = gpu.predict(states, t0, n_exp)
+    ref = O.predict(states, t0, ex)
+    near = np.isfinite(ref).all(-1) & (np.abs(ref - 1024).max(-1) < 1e4)
+    assert near.sum() >= n_exp
+    err = np.abs(xy[near] - ref[near]).max()
+    assert err <= POS_TOL, f"max position error {err:.3g} px"
+    assert gpu.stats()["kepler_failures"] == 0
+
+
+def test_force_free_motion_matches_oracle(gpu):
+    sky = _ragged_sky()
+    imgs = _images(sky, inject=False)
+    ndt.set_constants(gpu.ctx, 0.0, O.c_light(), O.obliquity())
+    gpu.load(sky.ex, imgs)
+    st = sky.states[::7]
+    xy = gpu.predict(st, sky.t0, sky.ex.n)
+    ref = O.predict(st, sky.t0, sky.ex, mu=0.0)
+    fin = np.isfinite(ref)
+    assert np.abs(xy[fin] - ref[fin]).max() <= POS_TOL
+    out = gpu.stack(st, sky.t0)
+    check_stack(out, O.stack(st, sky.t0, sky.ex, images=list(imgs), mu=0.0))
+
+
+# ------------------------------------------------------------------ stack ----
+
+@pytest.mark.parametrize("plane", ["f32"])
+def test_stack_ragged_matches_oracle(gpu, plane):
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs, plane=plane)
+    out = gpu.stack(sky.states, sky.t0)
+    ref = O.stack(sky.states, sky.t0, sky.ex, images=list(imgs))
+    rep = check_stack(out, ref)
+    assert rep["n_finite"] > 100
+    st = gpu.stats()
+    assert st["kepler_failures"] == 0
+    assert st["valid_samples"] == int(out["nobs"].sum())
+    assert st["samples"] == len(sky.states) * sky.ex.n
+
+
+def test_plain_workload_stack_and_top100(gpu):
+    """The tiny plain-method workload at its full size: 65,536 grid orbits,
+    10 exposures of 512 x 512, 5 injected sources, top-100."""
+    sky = synth.grid_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs)
+    out = gpu.stack(sky.states, sky.t0)
+    pl = [O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j]) for j in range(sky.ex.n)]
+    ref = O.stack(sky.states, sky.t0, sky.ex, planes=([p[0] for p in pl], [p[1] for p in pl]))
+    check_stack(out, ref)
+    idx, val = gpu.topk(100)
+    nu = O.snr(ref["Psi"], ref["Phi"], ref["nobs"])
+    check_topk(idx, val, nu, ref["n_amb"] > 0, 100)
+    assert set(sky.inj_orbit.tolist()) <= set(idx.tolist())
+    # a k larger than the number of finite nu: the tail is the lowest-index -inf orbits
+    idx2, val2 = gpu.topk(8192)
+    check_topk(idx2, val2, nu, ref["n_amb"] > 0, 8192)
+
+
+def _families(rng, n_orb, n_exp, n_fam):
+    cuts = np.sort(rng.choice(np.arange(1, n_orb), n_fam - 1, replace=False))
+    fo = np.concatenate([[0], cuts, [n_orb]]).astype(np.int64)
+    lists = []
+    for f in range(n_fam):
+        m = int(rng.integers(1, n_exp + 1))
+        lists.append(rng.choice(n_exp, m, replace=False).astype(np.int32))   # unsorted on purpose
+    fe = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
+    return fo, fe, np.concatenate(lists).astype(np.int32)
+
+
+@pytest.mark.parametrize("mode", ["plain", "persistent", "graph"])
+def test_families_match_oracle(gpu, mode):
+    sky = _ragged_sky(n_exp=9)
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs)
+    fam = _families(np.random.default_rng(2), len(sky.states), sky.ex.n, 37)
+    if mode != "plain":
+        ndt.set_launch(gpu.ctx, ndt.LAUNCH_PERSISTENT, 64, 8, use_graph=(mode == "graph"))
+    ref = O.stack(sky.states, sky.t0, sky.ex, images=list(imgs), families=fam)
+    for rep in range(2 if mode == "graph" else 1):   # the second graph call replays
+        out = gpu.stack(sky.states, sky.t0, families=fam)
+        check_stack(out, ref)
+    assert gpu.stats()["samples"] == int(sum((fam[0][f + 1] - fam[0][f]) * (fam[1][f + 1] - fam[1][f])
+                                             for f in range(len(fam[0]) - 1)))
+
+
+@pytest.mark.parametrize("ot", [32, 64, 128])
+@pytest.mark.parametrize("et", [8, 16, 32])
+def test_every_persistent_tile_shape(gpu, ot, et):
+    sky = _ragged_sky(n_exp=11)
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs)
+    ndt.set_launch(gpu.ctx, ndt.LAUNCH_PERSISTENT, ot, et)
+    out = gpu.stack(sky.states, sky.t0)
+    check_stack(out, O.stack(sky.states, sky.t0, sky.ex, images=list(imgs)))
+
+
+def test_host_pointers_give_device_results(gpu):
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs, host=True)
+    h = gpu.stack(sky.states, sky.t0, host=True)
+    hi, hv = gpu.topk(50, host=True)
+    gpu.load(sky.ex, imgs, host=False)
+    d = gpu.stack(sky.states, sky.t0)
+    di, dv = gpu.topk(50)
+    for k in h:
+        np.testing.assert_array_equal(h[k], d[k])
+    np.testing.assert_array_equal(hi, di)
+    np.testing.assert_array_equal(hv, dv)
+
+
+def test_per_pixel_variance_stack(gpu):
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    var = np.random.default_rng(4).uniform(0.5, 2.0, imgs.shape).astype(np.float32)
+    gpu.load(sky.ex, imgs, variances=var)
+    out = gpu.stack(sky.states, sky.t0)
+    check_stack(out, O.stack(sky.states, sky.t0, sky.ex, images=list(imgs), var_planes=list(var)))
+
+
+@pytest.mark.parametrize("plane", ["bf16", "f16"])
+def test_reduced_precision_stack_error(gpu, plane):
+    """Reduced-precision planes: nu error against the FP64 oracle stays within
+    the storage format's rounding, and the injected sources stay on top."""
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs, plane=plane)
+    out = gpu.stack(sky.states, sky.t0)
+    ref = O.stack(sky.states, sky.t0, sky.ex, images=list(imgs))
+    nu = O.snr(ref["Psi"], ref["Phi"], ref["nobs"])
+    clean = (ref["n_amb"] == 0) & np.isfinite(nu)
+    err = np.abs(out["snr"][clean] - nu[clean]) / np.maximum(1.0, np.abs(nu[clean]))
+    bound = 2.0 ** -7 if plane == "bf16" else 2.0 ** -10
+    assert err.max() <= bound, f"{plane}: max SNR error {err.max():.3g}"
+    idx, _ = gpu.topk(10)
+    assert set(sky.inj_orbit.tolist()) <= set(idx.tolist())
+
+
+# ------------------------------------------------------------ edge cases ----
+
+def test_degenerate_inputs(gpu):
+    sky = _ragged_sky()
+    imgs = _images(sky, inject=False)
+    with pytest.raises(ndt.NdtError) as e:
+        ndt.stack_orbits(gpu.ctx, gpu.soa(sky.states), sky.t0, len(sky.states))
+    assert e.value.status == ndt.ESTATE
+    gpu.load(sky.ex, imgs)
+    # empty batch
+    ndt.stack_orbits(gpu.ctx, gpu.soa(sky.states[:1]), sky.t0, 0)
+    with pytest.raises(ndt.NdtError) as e:
+        gpu.topk(5)
+    assert e.value.status == ndt.ESTATE
+    # an orbit that never lands in an image: nu = -inf, n_obs = 0
+    far = sky.states[:1].copy()
+    far[0, :3] *= -1.0
+    out = gpu.stack(far, sky.t0)
+    assert out["nobs"][0] == 0 and out["snr"][0] == -np.inf
+    idx, val = gpu.topk(3)
+    assert list(idx) == [0] and val[0] == -np.inf
+    # min_obs above every count: all -inf, ranking by index
+    out = gpu.stack(sky.states[:50], sky.t0, min_obs=1000)
+    assert np.all(out["snr"] == -np.inf)
+    idx, _ = gpu.topk(7)
+    assert list(idx) == list(range(7))
+    # bad arguments
+    bad = sky.ex.subset([0])
+    bad.sigma = np.array([0.0])
+    with pytest.raises(ndt.NdtError) as e:
+        gpu.load(bad, imgs[:1])
+    assert e.value.status == ndt.EINVAL
+    with pytest.raises(ndt.NdtError):
+        ndt.set_launch(gpu.ctx, ndt.LAUNCH_PERSISTENT, 48, 8)
+    fo = np.array([0, 10], np.int64)   # does not span the batch
+    with pytest.raises(ndt.NdtError) as e:
+        gpu.stack(sky.states[:20], sky.t0, families=(fo, np.array([0, 1], np.int64),
+                                                     np.array([0], np.int32)))
+    assert e.value.status == ndt.EINVAL
+
+
+def test_single_exposure_single_orbit(gpu):
+    sky = _ragged_sky()
+    imgs = _images(sky)
+    ex = sky.ex.subset([2])
+    gpu.load(ex, imgs[2:3])
+    st = sky.states[sky.inj_orbit[:1]]
+    out = gpu.stack(st, sky.t0)
+    check_stack(out, O.stack(st, sky.t0, ex, images=[imgs[2]]))
