@@ -128,8 +128,11 @@ void set_default_phys(ndt_ctx* c, double gm, double cl, double eps) {
   c->ph.gm = gm;
   c->ph.force_free = gm > 0.0 ? 0 : 1;
   c->ph.sqrt_gm = gm > 0.0 ? std::sqrt(gm) : 1.0;
+  c->ph.inv_sqrt_gm = 1.0 / c->ph.sqrt_gm;
   c->ph.inv_gm = gm > 0.0 ? 1.0 / gm : 0.0;
   c->ph.inv_c = cl > 0.0 ? (float)(1.0 / cl) : 0.0f;
+  c->ph.inv_c2 = cl > 0.0 ? (float)(1.0 / (cl * cl)) : 0.0f;
+  c->ph.gm_f = gm > 0.0 ? (float)gm : 0.0f;
   c->obliquity = eps;
 }
 

@@ -41,8 +41,11 @@ static_assert(sizeof(ExpDev) == 152, "ExpDev layout");
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
   double sqrt_gm;
+  double inv_sqrt_gm;
   double inv_gm;
   float inv_c;      // 1 / c (day/AU) for the light-time correction; 0: none
+  float inv_c2;     // 1 / c^2
+  float gm_f;       // GM_sun in FP32 (light-time acceleration term)
   int32_t force_free;
 };
 
@@ -68,6 +71,21 @@ struct CSum {
   }
   __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
 };
+
+// ---------------------------------------------------------------------------
+// FP64 reciprocal by Newton-Raphson refinement of an FP32 seed (the classical
+// iteration y <- y + y (1 - x y), which squares the relative error; e.g.
+// Knuth, TAOCP vol. 2, sec. 4.3.3).  The seed is the FP32 reciprocal
+// (relative error < 2^-23); one step gives < 2^-45, two steps reach FP64
+// rounding.  Valid for |x| within the FP32 normal range.
+// ---------------------------------------------------------------------------
+template <int STEPS>
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y = (double)__frcp_rn((float)x);
+#pragma unroll
+  for (int i = 0; i < STEPS; ++i) y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
 
 // ---------------------------------------------------------------------------
 // Stumpff functions C(z) = sum (-z)^k/(2k+2)!, S(z) = sum (-z)^k/(2k+3)!.
@@ -103,7 +121,9 @@ __device__ __forceinline__ void stumpff_series(double z, double& C, double& S) {
 
 __device__ __forceinline__ void stumpff(double z, double& C, double& S) {
   const double az = fabs(z);
-  if (az < 1e-3) {
+  if (az < 1e-6) {
+    stumpff_series<3>(z, C, S);
+  } else if (az < 1e-3) {
     stumpff_series<4>(z, C, S);
   } else if (az < 0.05) {
     stumpff_series<6>(z, C, S);
@@ -130,6 +150,7 @@ struct OrbitConst {
   double alpha;        // 2/r - v^2/GM (reciprocal semi-major axis), conserved
   double period;       // orbital period (bound orbits), else 0
   double inv_period;
+  double half_period;  // steps longer than this are reduced modulo the period
 };
 
 __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
@@ -141,9 +162,11 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     double n = ph.sqrt_gm * oc.alpha * sqrt(oc.alpha);   // mean motion
     oc.period = 6.283185307179586476925 / n;
     oc.inv_period = n / 6.283185307179586476925;
+    oc.half_period = 0.5 * oc.period;
   } else {
     oc.period = 0.0;
     oc.inv_period = 0.0;
+    oc.half_period = 1e300;
   }
   return oc;
 }
@@ -156,12 +179,19 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
 // eq. 4.4-14) is solved by the Laguerre-Conway iteration (Conway 1986) from a
 // third-order series guess in dt.  F, F' and F'' are evaluated in FP64; only
 // the correction ratio is formed in FP32, so every iterate is an FP64 value
-// and the converged root satisfies F = 0 to FP64 rounding.  The iteration
-// stops once the correction is below 1e-9; the Lagrange coefficients are then
-// corrected to first order in that last step instead of re-evaluating the
-// Stumpff functions (the second-order remainder is below 1e-17).
+// and the converged root satisfies F = 0 to FP64 rounding.
+//
+// The iteration stops at the first evaluation whose correction delta is below
+// kKeplerStop; the Lagrange coefficients are then taken at chi - delta to
+// first order in delta (their derivatives in chi are already at hand), so the
+// Stumpff functions are never re-evaluated.  The second-order remainder is
+// (delta^2 / 2) |d^2 f / d chi^2| r0 <= (1e-14 / 2) * 0.5 * r0, below 1e-14 AU
+// for r0 < 4 AU and 1e-13 AU at 50 AU.  With the series guess the first
+// evaluation already meets this for steps up to a few days.
 // Returns the number of evaluations, or -1 when kMaxKeplerIters is reached.
 // ---------------------------------------------------------------------------
+constexpr float kKeplerStop = 1e-7f;
+
 __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc, double dt,
                                            double r[3], double v[3], double& rn, double& inv_r) {
   if (ph.force_free) {
@@ -170,15 +200,15 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     inv_r = 1.0 / rn;
     return 0;
   }
-  if (oc.alpha > 0.0) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
+  if (fabs(dt) > oc.half_period) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
   const double alpha = oc.alpha;
-  const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) / ph.sqrt_gm;
+  const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ph.inv_sqrt_gm;
   const double a1 = fma(-alpha, rn, 1.0);            // 1 - alpha r0
   const double sdt = ph.sqrt_gm * dt;
   // third-order series of chi(dt): u - sig0 u^2/(2 r0) - u^3/6 (1/r0 - alpha - 3 sig0^2/r0^2)
   const double u = sdt * inv_r;
-  double chi = u - 0.5 * sig0 * inv_r * u * u -
-               (u * u * u / 6.0) * (inv_r - alpha - 3.0 * sig0 * sig0 * inv_r * inv_r);
+  const double si = sig0 * inv_r;
+  double chi = u * fma(u, fma(-(u / 6.0), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
   if (fabs(alpha) * chi * chi > 0.25 || !(fabs(chi) < 1e30)) {
     chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
   }
@@ -191,22 +221,23 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     const double chi2C = chi2 * C;
     const double chi3S = chi2 * chi * S;
     const double chi1mzS = chi * fma(-z, S, 1.0);
+    const double omzC = fma(-z, C, 1.0);
     const double F = fma(sig0, chi2C, fma(a1, chi3S, fma(rn, chi, -sdt)));
     const double dF = fma(sig0, chi1mzS, fma(a1, chi2C, rn));        // = |r|
-    const double d2F = fma(sig0, fma(-z, C, 1.0), a1 * chi1mzS);
+    const double d2F = fma(sig0, omzC, a1 * chi1mzS);
     const float Ff = (float)F, dFf = (float)dF, d2Ff = (float)d2F;
     const float disc = fabsf(16.0f * dFf * dFf - 20.0f * Ff * d2Ff);
     const float delta = 5.0f * Ff / (dFf + sqrtf(disc));
-    if (fabsf(delta) <= 1e-9f) {
+    if (fabsf(delta) <= kKeplerStop) {
       // outputs at chi - delta, to first order in delta
       const double d = (double)delta;
       const double chi2C_c = fma(-d, chi1mzS, chi2C);
-      const double f = 1.0 - chi2C_c * inv_r;
-      const double g = dt - fma(-d, chi2C, chi3S) / ph.sqrt_gm;
+      const double f = fma(-chi2C_c, inv_r, 1.0);
+      const double g = fma(-fma(-d, chi2C, chi3S), ph.inv_sqrt_gm, dt);
       const double rc = fma(-d, d2F, dF);
-      const double inv_rc = 1.0 / rc;
-      const double fdot = -ph.sqrt_gm * fma(-d, fma(-z, C, 1.0), chi1mzS) * inv_rc * inv_r;
-      const double gdot = 1.0 - chi2C_c * inv_rc;
+      const double inv_rc = rcp_nr<2>(rc);
+      const double fdot = -ph.sqrt_gm * fma(-d, omzC, chi1mzS) * (inv_rc * inv_r);
+      const double gdot = fma(-chi2C_c, inv_rc, 1.0);
       double rr[3];
       for (int i = 0; i < 3; ++i) rr[i] = fma(f, r[i], g * v[i]);
       for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], gdot * v[i]);
@@ -222,50 +253,52 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
 
 // ---------------------------------------------------------------------------
 // Light-time corrected topocentric vector.  With (r, v) the geometric state
-// at the exposure epoch, the emitted position is expanded to second order in
-// the light time tau: r(t - tau) = r - tau v - (tau^2 / 2) GM r / |r|^3 (the
-// third-order term is below 1e-11 AU for every orbit class in the
-// workloads).  tau is found by one fixed-point refinement of tau = |rho| / c
-// starting from the geometric distance; tau only needs ~1e-7 relative
-// accuracy, so its square roots are FP32.
+// at the exposure epoch and d = r - r_obs, the emitted position is expanded
+// to second order in the light time tau:
+//   rho = d - tau v - (tau^2 / 2) GM r / |r|^3
+// (the third-order term is below 1e-11 AU for every orbit class in the
+// workloads).  tau solves tau = |rho| / c; starting from tau0 = |d| / c, one
+// fixed-point step gives tau1 = tau0 - (d . v) / c^2 to relative accuracy
+// (v/c)^2 ~ 1e-8, which moves rho by under 1e-11 AU.  tau only needs ~1e-7
+// relative accuracy, so it is carried in FP32; rho itself is FP64.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], const double v[3],
                                              double inv_r, const double obs[3], double rho[3]) {
-  double d[3] = {r[0] - obs[0], r[1] - obs[1], r[2] - obs[2]};
+  const double d[3] = {r[0] - obs[0], r[1] - obs[1], r[2] - obs[2]};
   if (ph.inv_c == 0.0f) {
     rho[0] = d[0]; rho[1] = d[1]; rho[2] = d[2];
     return;
   }
-  const double kacc = ph.force_free ? 0.0 : -0.5 * ph.gm * inv_r * inv_r * inv_r;
-  float tau = __fsqrt_rn((float)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2])) * ph.inv_c;
-  for (int pass = 0; pass < 2; ++pass) {
-    const double t = (double)tau;
-    const double h = kacc * t * t;   // -(tau^2/2) GM / |r|^3
-    for (int i = 0; i < 3; ++i) rho[i] = fma(h, r[i], fma(-t, v[i], d[i]));
-    if (pass == 0)
-      tau = __fsqrt_rn((float)(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2])) * ph.inv_c;
-  }
+  const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
+  const float tau = fmaf(-(float)dv, ph.inv_c2, __fsqrt_rn((float)dd) * ph.inv_c);
+  const float irf = (float)inv_r;
+  const float hf = ph.force_free ? 0.0f : -0.5f * ph.gm_f * irf * irf * irf * tau * tau;
+  const double t = (double)tau, h = (double)hf;
+  for (int i = 0; i < 3; ++i) rho[i] = fma(h, r[i], fma(-t, v[i], d[i]));
 }
 
 // TAN projection through the precomputed per-exposure rows (Calabretta &
 // Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
 // Returns false when cos c <= 0.
+// The reciprocal of rho . p0 needs ~1e-12 relative accuracy (x within 1e-8 px
+// at 4096 px from CRPIX): one Newton step from the FP32 seed gives < 2^-45.
 __device__ __forceinline__ bool project(const ExpDev& e, const double rho[3], double& x, double& y) {
   const double den = rho[0] * e.p0[0] + rho[1] * e.p0[1] + rho[2] * e.p0[2];
-  if (!(den > 0.0)) return false;
-  const double inv = 1.0 / den;
+  if (!(den > 1e-30)) return false;
+  const double inv = rcp_nr<1>(den);
   x = fma(rho[0] * e.ax[0] + rho[1] * e.ax[1] + rho[2] * e.ax[2], inv, e.crpix[0]);
   y = fma(rho[0] * e.ay[0] + rho[1] * e.ay[1] + rho[2] * e.ay[2], inv, e.crpix[1]);
   return true;
 }
 
 // Nearest pixel (pixel i spans [i - 1/2, i + 1/2)); false outside the image.
+// (the conversion saturates far outside the int range, which stays outside
+// the image; x and y are finite whenever project() succeeded)
 __device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double x, double y, int& ix, int& iy) {
-  const double fx = floor(x + 0.5), fy = floor(y + 0.5);
-  if (!(fx >= 0.0 && fx < (double)e.W && fy >= 0.0 && fy < (double)e.H)) return false;
-  ix = (int)fx;
-  iy = (int)fy;
-  return true;
+  ix = __double2int_rd(x + 0.5);
+  iy = __double2int_rd(y + 0.5);
+  return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
 }
 
 template <int PT>
