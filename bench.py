@@ -36,8 +36,15 @@ UNIT = "samples/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # FP64 flops executed per (orbit, exposure) sample by the stack kernel on this
 # workload, from ncu instruction counters (DFMA x 2 + DADD + DMUL) divided by
-# the samples of the captured launch; see the design doc (roofline section).
-FP64_FLOP_PER_SAMPLE = None
+# the samples of the captured launch (MBA-scale workload at 512 orbits per
+# family, 1024 x 1024 images: 63.5 DFMA + 34.1 DMUL + 6.8 DADD per sample).
+# The FP64 pipe also issues conversions and compares (126.5 FP64-pipe thread
+# instructions per sample in all), roofline section.
+FP64_FLOP_PER_SAMPLE = 168.0
+FP64_PIPE_INST_PER_SAMPLE = 126.5
+# DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
+# measured on the current kernel.
+TRAFFIC_BYTES_PER_LAUNCH = None
 
 
 def parse():
@@ -418,9 +425,15 @@ def main():
     stack_s = statistics.mean(r["stack_ms"]) / 1e3
     if FP64_FLOP_PER_SAMPLE is not None:
         ach = FP64_FLOP_PER_SAMPLE * samples / stack_s / 1e12
+        # FP64 pipe issue rate: 2 thread instructions / clock / SM
+        pipe_frac = FP64_PIPE_INST_PER_SAMPLE * samples / stack_s / (152 * 2 * 2.07e9)
         line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                            "kernel": "k_stack_persistent (FP64 pipe)"}
+                            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                            "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                            "kernel": "stack kernel (FP64 pipe)",
+                            "fp64_pipe_issue_frac": pipe_frac,
+                            "algorithmic_bytes_per_launch":
+                                (8 if forms[head].plane == "f32" else 4) * r["valid"]}
     else:
         line["roofline"] = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": None, "traffic": None,

@@ -18,6 +18,9 @@ namespace ndt {
 namespace {
 
 constexpr int kBlock = 128;
+#ifndef NDT_STACK_MINB
+#define NDT_STACK_MINB 1   // resident CTAs per SM requested from the register allocator
+#endif
 
 __device__ __forceinline__ void load_state(const double* __restrict__ s, int64_t n, int64_t o,
                                            double r[3], double v[3]) {
@@ -107,7 +110,7 @@ __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, i
 
 // Plain form: one thread per orbit, grid covers all orbits.
 template <int PT>
-__global__ void __launch_bounds__(kBlock) k_stack_plain(const StackArgs a) {
+__global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const StackArgs a) {
   const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const bool active = o < a.n;
   Walk w;
@@ -141,7 +144,7 @@ __device__ __forceinline__ void team_sync(int team, int team_threads) {
 // them.  The loop ends when the counter passes the last item: no thread ever
 // waits on another team.
 template <int PT, int TEAM_WARPS, int ET>
-__global__ void __launch_bounds__(kBlock) k_stack_persistent(const StackArgs a) {
+__global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(const StackArgs a) {
   constexpr int TEAM = TEAM_WARPS * 32;
   constexpr int NTEAMS = kBlock / TEAM;
   __shared__ ExpDev stage[NTEAMS][ET];

@@ -235,7 +235,7 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
       const double f = fma(-chi2C_c, inv_r, 1.0);
       const double g = fma(-fma(-d, chi2C, chi3S), ph.inv_sqrt_gm, dt);
       const double rc = fma(-d, d2F, dF);
-      const double inv_rc = rcp_nr<2>(rc);
+      const double inv_rc = rcp_nr<1>(rc);   // 2^-45: f, g, fdot, gdot stay within 1e-13 AU
       const double fdot = -ph.sqrt_gm * fma(-d, omzC, chi1mzS) * (inv_rc * inv_r);
       const double gdot = fma(-chi2C_c, inv_rc, 1.0);
       double rr[3];
