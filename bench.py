@@ -44,7 +44,7 @@ FP64_FLOP_PER_SAMPLE = 168.0
 FP64_PIPE_INST_PER_SAMPLE = 126.5
 # DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
 # measured on the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_BYTES_PER_LAUNCH = 1.86e9 + 72e6   # full-size launch, ncu 1-pass dram__bytes
 
 
 def parse():

@@ -201,6 +201,55 @@ ndt_status ndt_autotune(ndt_ctx *ctx, const double *states, double t0, int64_t n
                         const int64_t *fam_orbit_off, const int64_t *fam_exp_off,
                         const int32_t *fam_exp_idx, int32_t n_fam, float *times_ms);
 
+/*
+ * Learned vetting (paper sec. 5.2.3: a neural network that recognises
+ * prepared image stacks of true and false positives, left there as future
+ * work; the stamp and the network below are this library's reading).
+ *
+ * stamps: for each candidate (an index into the orbit batch `states`, SoA
+ * 6 x n_orbits at epoch t0) and each loaded exposure where its predicted
+ * nearest pixel is inside the image, accumulate over a 21 x 21 window centred
+ * on that pixel: SPsi, SPhi, Q = sum psi^2/phi and the count n per window
+ * pixel.  Channel 0 = SPsi/sqrt(SPhi) (stacked SNR, 0 where SPhi = 0);
+ * channel 1 = (Q - SPsi^2/SPhi - (n-1)) / sqrt(2 (n-1)), the constant-flux
+ * chi-square excess (0 where n < 2).  Layout [n_cand][2][21][21]; stamps_f32
+ * (FP32) and stamps_bf16 (BF16 bit patterns, RNE) may each be NULL.
+ * Candidate indices outside [0, n_orbits) give all-zero stamps.
+ */
+ndt_status ndt_stamps(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
+                      const int64_t *cand_idx, int64_t n_cand, float *stamps_f32,
+                      uint16_t *stamps_bf16);
+
+/* Number of parameters of the vetting network: 52,929.  Flat FP32 layout:
+   w1 [32][2][5][5], b1 [32], w2 [32][32][5][5], b2 [32], w3 [32][32][5][5],
+   b3 [32], wl [32], bl [1].  The network: three 5x5 "same" cross-correlation
+   layers with bias and ReLU (2->32->32->32 channels), global average pool,
+   linear 32->1 giving a logit. */
+int64_t ndt_cnn_param_count(void);
+
+/* Logits of n BF16 stamps [n][2][21][21] (FP32 accumulation). */
+ndt_status ndt_cnn_forward(ndt_ctx *ctx, const float *params, const uint16_t *stamps_bf16,
+                           int64_t n, float *logits);
+
+/* Mean binary cross-entropy with logits over the n stamps (labels 0 or 1)
+   and its gradient with respect to every parameter (grad: 52,929 FP32,
+   overwritten).  loss_out and logits_out may be NULL. */
+ndt_status ndt_cnn_loss_grad(ndt_ctx *ctx, const float *params, const uint16_t *stamps_bf16,
+                             const float *labels, int64_t n, float *grad, float *loss_out,
+                             float *logits_out);
+
+/* One Adam step (Kingma & Ba 2015, bias-corrected, step >= 1) on device
+   arrays params, m, v given the gradient grad (all n_params FP32, device
+   memory only). */
+ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, float *m, float *v,
+                             int64_t n_params, int32_t step, float lr, float beta1, float beta2,
+                             float eps);
+
+/* vet: stamps of the candidates (as ndt_stamps) scored by the network:
+   scores[i] = sigmoid(logit) in [0, 1]. */
+ndt_status ndt_vet(ndt_ctx *ctx, const float *params, const double *states, double t0,
+                   int64_t n_orbits, const int64_t *cand_idx, int64_t n_cand, float *scores);
+
 /* Copy the context's counters into *out. */
 ndt_status ndt_get_stats(ndt_ctx *ctx, ndt_stats *out);
 

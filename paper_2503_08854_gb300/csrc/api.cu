@@ -69,6 +69,9 @@ struct ndt_ctx {
   DevBuf queue_head, counters;
   // top-k
   DevBuf topk_scratch, topk_out;
+  // vetting
+  DevBuf cand_stage, stamp_pos, stamp_f32, stamp_bf16, cnn_x, cnn_labels, cnn_out, cnn_scratch,
+      cnn_params, cnn_grad;
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   cudaGraphExec_t graph = nullptr;
@@ -222,7 +225,9 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->absmax_dev, &c->scales_dev, &c->stage_images, &c->stage_vars,
                     &c->stage_states, &c->snr, &c->out_tmp, &c->xy_tmp, &c->fam_orb_off,
                     &c->fam_exp_off, &c->fam_exp_pos, &c->item_off, &c->fam_order,
-                    &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out};
+                    &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
+                    &c->cand_stage, &c->stamp_pos, &c->stamp_f32, &c->stamp_bf16, &c->cnn_x,
+                    &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad};
   for (DevBuf* b : bufs) b->release();
   delete c;
 }
@@ -728,6 +733,186 @@ ndt_status ndt_autotune(ndt_ctx* ctx, const double* states, double t0, int64_t n
   ctx->use_graph = saved_graph;
   ctx->orbit_tile = best_ot;
   ctx->exp_tile = best_et;
+  return NDT_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ vetting ----
+
+namespace {
+
+// Output buffer on the device: `user` itself when it is device memory, else a
+// context scratch that is copied back by copy_out().
+template <class T>
+ndt_status out_buffer(ndt_ctx* ctx, T* user, size_t count, DevBuf& scratch, T** dev) {
+  if (!user || is_device_ptr(user)) {
+    *dev = user;
+    return NDT_OK;
+  }
+  NDT_CK(scratch.ensure(sizeof(T) * count), "output scratch");
+  *dev = static_cast<T*>(scratch.p);
+  return NDT_OK;
+}
+
+template <class T>
+ndt_status copy_out(ndt_ctx* ctx, T* user, const T* dev, size_t count) {
+  if (user && user != dev)
+    NDT_CK(cudaMemcpyAsync(user, dev, sizeof(T) * count, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  return NDT_OK;
+}
+
+ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                       const int64_t* cand_idx, int64_t n_cand, float* f32_dev,
+                       __nv_bfloat16* bf16_dev) {
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "stamps before load_exposures");
+  if (n_orbits < 0 || n_cand < 0 || (n_cand > 0 && (!states || !cand_idx)))
+    return fail(ctx, NDT_EINVAL, "bad stamp arguments");
+  if (n_cand == 0) return NDT_OK;
+  const void* st_dev = nullptr;
+  ndt_status s = to_device(ctx, states, sizeof(double) * 6 * n_orbits, ctx->stage_states, &st_dev);
+  if (s != NDT_OK) return s;
+  const void* cd = nullptr;
+  s = to_device(ctx, cand_idx, sizeof(int64_t) * n_cand, ctx->cand_stage, &cd);
+  if (s != NDT_OK) return s;
+  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp), "stamp positions");
+  NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0,
+                                static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
+                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(),
+                                ctx->counters.as<unsigned long long>(), ctx->stream), "stamp positions");
+  NDT_CK(launch_stamps(ctx->stamp_pos.as<int2>(), n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp,
+                       ctx->planes.p, ctx->plane_type, f32_dev, bf16_dev, ctx->n_sms, ctx->stream),
+         "stamp kernel");
+  ctx->launches += 2;
+  return NDT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ndt_status ndt_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                      const int64_t* cand_idx, int64_t n_cand, float* stamps_f32,
+                      uint16_t* stamps_bf16) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const size_t cnt = (size_t)n_cand * 2 * 441;
+  float* f = nullptr;
+  uint16_t* b = nullptr;
+  ndt_status s = out_buffer(ctx, stamps_f32, cnt, ctx->stamp_f32, &f);
+  if (s == NDT_OK) s = out_buffer(ctx, stamps_bf16, cnt, ctx->stamp_bf16, &b);
+  if (s == NDT_OK)
+    s = make_stamps(ctx, states, t0, n_orbits, cand_idx, n_cand, f,
+                    reinterpret_cast<__nv_bfloat16*>(b));
+  if (s != NDT_OK) return s;
+  if ((s = copy_out(ctx, stamps_f32, f, cnt)) != NDT_OK) return s;
+  if ((s = copy_out(ctx, stamps_bf16, b, cnt)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+int64_t ndt_cnn_param_count(void) { return cnn_param_count(); }
+
+ndt_status ndt_cnn_forward(ndt_ctx* ctx, const float* params, const uint16_t* stamps_bf16,
+                           int64_t n, float* logits) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (n < 0 || (n > 0 && (!params || !stamps_bf16 || !logits))) return fail(ctx, NDT_EINVAL, "bad CNN arguments");
+  if (n == 0) return NDT_OK;
+  const void* th = nullptr;
+  const void* x = nullptr;
+  ndt_status s = to_device(ctx, params, sizeof(float) * cnn_param_count(), ctx->cnn_params, &th);
+  if (s == NDT_OK) s = to_device(ctx, stamps_bf16, sizeof(uint16_t) * 2 * 441 * n, ctx->cnn_x, &x);
+  float* lo = nullptr;
+  if (s == NDT_OK) s = out_buffer(ctx, logits, n, ctx->cnn_out, &lo);
+  if (s != NDT_OK) return s;
+  NDT_CK(launch_cnn_forward(static_cast<const float*>(th), static_cast<const __nv_bfloat16*>(x), n, lo,
+                            ctx->n_sms, ctx->stream), "CNN forward");
+  ctx->launches += 1;
+  if ((s = copy_out(ctx, logits, lo, n)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status ndt_cnn_loss_grad(ndt_ctx* ctx, const float* params, const uint16_t* stamps_bf16,
+                             const float* labels, int64_t n, float* grad, float* loss_out,
+                             float* logits_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (n < 1 || !params || !stamps_bf16 || !labels || !grad)
+    return fail(ctx, NDT_EINVAL, "bad CNN arguments");
+  const int np = cnn_param_count();
+  const void *th = nullptr, *x = nullptr, *lab = nullptr;
+  ndt_status s = to_device(ctx, params, sizeof(float) * np, ctx->cnn_params, &th);
+  if (s == NDT_OK) s = to_device(ctx, stamps_bf16, sizeof(uint16_t) * 2 * 441 * n, ctx->cnn_x, &x);
+  if (s == NDT_OK) s = to_device(ctx, labels, sizeof(float) * n, ctx->cnn_labels, &lab);
+  float* g = nullptr;
+  if (s == NDT_OK) s = out_buffer(ctx, grad, np, ctx->cnn_grad, &g);
+  if (s != NDT_OK) return s;
+  // scratch: loss (1 float, padded) + logits (n) + one a1 plane set per CTA
+  const int blocks = cnn_backward_blocks(n, ctx->n_sms);
+  NDT_CK(ctx->cnn_scratch.ensure(sizeof(float) * (16 + n + (size_t)blocks * 32 * 441)), "CNN scratch");
+  float* loss_d = ctx->cnn_scratch.as<float>();
+  float* logit_d = loss_d + 16;
+  float* a1 = logit_d + n;
+  NDT_CK(cudaMemsetAsync(g, 0, sizeof(float) * np, ctx->stream), "memset");
+  NDT_CK(cudaMemsetAsync(loss_d, 0, sizeof(float), ctx->stream), "memset");
+  NDT_CK(launch_cnn_backward(static_cast<const float*>(th), static_cast<const __nv_bfloat16*>(x),
+                             static_cast<const float*>(lab), n, g, loss_d, a1, logit_d, ctx->n_sms,
+                             ctx->stream), "CNN backward");
+  ctx->launches += 1;
+  if ((s = copy_out(ctx, grad, g, np)) != NDT_OK) return s;
+  if (loss_out) {
+    if (is_device_ptr(loss_out))
+      NDT_CK(cudaMemcpyAsync(loss_out, loss_d, 4, cudaMemcpyDeviceToDevice, ctx->stream), "copy");
+    else
+      NDT_CK(cudaMemcpyAsync(loss_out, loss_d, 4, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  }
+  if (logits_out)
+    NDT_CK(cudaMemcpyAsync(logits_out, logit_d, sizeof(float) * n,
+                           is_device_ptr(logits_out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           ctx->stream), "copy");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status ndt_cnn_adam_step(ndt_ctx* ctx, float* params, const float* grad, float* m, float* v,
+                             int64_t n_params, int32_t step, float lr, float beta1, float beta2,
+                             float eps) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (n_params < 1 || n_params > (1 << 30) || step < 1 || !(lr > 0.0f))
+    return fail(ctx, NDT_EINVAL, "bad Adam arguments");
+  if (!is_device_ptr(params) || !is_device_ptr(grad) || !is_device_ptr(m) || !is_device_ptr(v))
+    return fail(ctx, NDT_EINVAL, "Adam state must be device memory");
+  NDT_CK(launch_adam(params, grad, m, v, (int)n_params, lr, beta1, beta2, eps, step, ctx->stream),
+         "Adam kernel");
+  ctx->launches += 1;
+  return NDT_OK;
+}
+
+ndt_status ndt_vet(ndt_ctx* ctx, const float* params, const double* states, double t0,
+                   int64_t n_orbits, const int64_t* cand_idx, int64_t n_cand, float* scores) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (n_cand < 0 || (n_cand > 0 && (!params || !scores))) return fail(ctx, NDT_EINVAL, "bad vet arguments");
+  if (n_cand == 0) return NDT_OK;
+  NDT_CK(ctx->stamp_bf16.ensure(sizeof(uint16_t) * 2 * 441 * n_cand), "stamp buffer");
+  ndt_status s = make_stamps(ctx, states, t0, n_orbits, cand_idx, n_cand, nullptr,
+                             ctx->stamp_bf16.as<__nv_bfloat16>());
+  if (s != NDT_OK) return s;
+  const void* th = nullptr;
+  s = to_device(ctx, params, sizeof(float) * cnn_param_count(), ctx->cnn_params, &th);
+  float* lo = nullptr;
+  if (s == NDT_OK) s = out_buffer(ctx, scores, n_cand, ctx->cnn_out, &lo);
+  if (s != NDT_OK) return s;
+  NDT_CK(launch_cnn_forward(static_cast<const float*>(th), ctx->stamp_bf16.as<__nv_bfloat16>(), n_cand,
+                            lo, ctx->n_sms, ctx->stream), "CNN forward");
+  NDT_CK(launch_sigmoid(lo, n_cand, ctx->stream), "sigmoid");
+  ctx->launches += 2;
+  if ((s = copy_out(ctx, scores, lo, n_cand)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
   return NDT_OK;
 }
 

@@ -375,6 +375,25 @@ cudaError_t launch_predict(const double* states, int64_t n, double t0, const Exp
                            const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph,
                            double* xy, unsigned long long* counters, cudaStream_t st);
 
+// vetting (stamps + CNN)
+int cnn_param_count();
+size_t cnn_smem_bytes();
+int cnn_backward_blocks(int64_t n, int n_sms);
+cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, const int64_t* cand,
+                                   int64_t n_cand, const ExpDev* ex, int32_t n_exp, Phys ph,
+                                   int2* pos, unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+                          const void* planes, int plane_type, float* out_f32,
+                          __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st);
+cudaError_t launch_cnn_forward(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
+                               int n_sms, cudaStream_t st);
+cudaError_t launch_cnn_backward(const float* th, const __nv_bfloat16* x, const float* labels,
+                                int64_t n, float* grad, float* loss_sum, float* a1_scratch,
+                                float* logits, int n_sms, cudaStream_t st);
+cudaError_t launch_sigmoid(float* z, int64_t n, cudaStream_t st);
+cudaError_t launch_adam(float* th, const float* g, float* m, float* v, int n, float lr, float b1,
+                        float b2, float eps, int step, cudaStream_t st);
+
 // top-k
 struct TopkScratch {
   unsigned int* hist;          // 256 bins

@@ -62,6 +62,14 @@ _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
 _lib.ndt_get_stats.argtypes = [_vp, C.POINTER(Stats)]
+_lib.ndt_stamps.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, _vp, _vp]
+_lib.ndt_cnn_param_count.argtypes = []
+_lib.ndt_cnn_param_count.restype = _i64
+_lib.ndt_cnn_forward.argtypes = [_vp, _vp, _vp, _i64, _vp]
+_lib.ndt_cnn_loss_grad.argtypes = [_vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]
+_lib.ndt_cnn_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i32, C.c_float, C.c_float,
+                                   C.c_float, C.c_float]
+_lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 
 
@@ -203,9 +211,44 @@ def synchronize(ctx):
     _check(ctx, _lib.ndt_synchronize(ctx))
 
 
+def stamps(ctx, states_soa, t0, n_orbits, cand_idx, stamps_f32=None, stamps_bf16=None):
+    """Stacked stamps [n_cand][2][21][21] of candidates (indices into the batch)."""
+    _check(ctx, _lib.ndt_stamps(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(cand_idx),
+                                int(len(cand_idx)), _ptr(stamps_f32), _ptr(stamps_bf16)))
+
+
+def cnn_param_count():
+    return int(_lib.ndt_cnn_param_count())
+
+
+def cnn_forward(ctx, params, stamps_bf16, n, logits):
+    _check(ctx, _lib.ndt_cnn_forward(ctx, _ptr(params), _ptr(stamps_bf16), int(n), _ptr(logits)))
+
+
+def cnn_loss_grad(ctx, params, stamps_bf16, labels, n, grad, logits=None):
+    """Mean BCE loss (returned) and its gradient (written to ``grad``)."""
+    loss = np.zeros(1, np.float32)
+    _check(ctx, _lib.ndt_cnn_loss_grad(ctx, _ptr(params), _ptr(stamps_bf16), _ptr(labels), int(n),
+                                       _ptr(grad), _ptr(loss), _ptr(logits)))
+    return float(loss[0])
+
+
+def cnn_adam_step(ctx, params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    _check(ctx, _lib.ndt_cnn_adam_step(ctx, _ptr(params), _ptr(grad), _ptr(m), _ptr(v),
+                                       int(params.numel() if hasattr(params, "numel") else len(params)),
+                                       int(step), lr, beta1, beta2, eps))
+
+
+def vet(ctx, params, states_soa, t0, n_orbits, cand_idx, scores):
+    """Stamps of the candidates scored by the network (sigmoid outputs)."""
+    _check(ctx, _lib.ndt_vet(ctx, _ptr(params), _ptr(states_soa), float(t0), int(n_orbits),
+                             _ptr(cand_idx), int(len(cand_idx)), _ptr(scores)))
+
+
 def exported_symbols():
     """Names of the C entry points this binding uses (all must be exported)."""
     return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
             "ndt_load_exposures", "ndt_stack_orbits", "ndt_topk_candidates",
             "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_autotune",
-            "ndt_get_stats", "ndt_synchronize"]
+            "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
+            "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet"]

@@ -325,3 +325,62 @@ def render_sources_torch(images, xy, flux, sigma, radius=6.0):
         lin = (Y[m] * W + X[m]).long()
         images[j].view(-1).index_add_(0, lin, val[m].to(images.dtype))
     return images
+
+
+# --------------------------------------------------------------------------
+# Vetting survey (training and evaluation stamps for the learned vetter)
+# --------------------------------------------------------------------------
+
+def field_states(rng, n, lon, r_range=(2.3, 2.7), dv_kms=0.4, spread=2e-3):
+    """Orbits near a tracked field: heliocentric distance r ~ U(r_range), a
+    random angular offset (up to ``spread`` rad in longitude and latitude) from
+    the field's reference direction at t0, circular prograde speed plus
+    radial/tangential offsets ~ U(-dv, dv) km/s."""
+    r = rng.uniform(*r_range, n)
+    dl = rng.uniform(-spread, spread, n)
+    db = rng.uniform(-spread, spread, n)
+    L = lon + dl
+    rh = np.stack([np.cos(L) * np.cos(db), np.sin(L) * np.cos(db), np.sin(db)], -1)
+    th = np.stack([-np.sin(L), np.cos(L), np.zeros(n)], -1)
+    vr = rng.uniform(-dv_kms, dv_kms, n) * KMS_TO_AUD
+    vt = rng.uniform(-dv_kms, dv_kms, n) * KMS_TO_AUD
+    vc = GAUSS_K / np.sqrt(r)
+    pos = r[:, None] * rh
+    vel = vr[:, None] * rh + (vc + vt)[:, None] * th
+    return np.concatenate([pos, vel], 1)
+
+
+def vetting_sky(*, seed, n_exp=10, nights=20.0, size=1024, scale_arcsec=2.0, n_src=400,
+                n_art=400, n_rand=400, lon=0.7, snr_range=(3.0, 10.0), art_snr=(8.0, 25.0)) -> Sky:
+    """Tracked field like the tiny plain-method workload (10 epochs over 20
+    nights, pointings following a 2.5 AU circular body), larger and coarser so
+    that hundreds of sources stay inside.  Draws: ``n_src`` injected asteroids
+    with stacked SNR ~ U(snr_range) over the n_exp exposures (the per-image
+    flux is the stacked SNR / sqrt(n_exp)); ``n_art`` single-exposure
+    artefacts (an orbit, one exposure index and a per-image SNR ~ U(art_snr));
+    ``n_rand`` unrelated random orbits.  meta holds the artefact and random
+    orbits."""
+    rng = np.random.default_rng(seed)
+    step = nights / n_exp
+    mjd = 60000.5 + step * np.arange(n_exp) + rng.uniform(-0.1, 0.1, n_exp)
+    t0 = float(60000.5 + step * (n_exp - 1) / 2.0)
+    obs = observer_position(mjd, t0, lon)
+    crval = tracking_pointings(mjd, obs, t0, 2.5, lon)
+    s = scale_arcsec / 3600.0
+    sigma = rng.uniform(1.3, 1.8, n_exp).astype(np.float32).astype(np.float64)
+    ex = Exposures(mjd=mjd, obs=obs, crval=crval,
+                   crpix=np.tile(np.array([size / 2.0, size / 2.0]), (n_exp, 1)),
+                   cd=np.tile(np.array([[-s, 0.0], [0.0, s]]), (n_exp, 1, 1)), sigma=sigma,
+                   var=np.ones(n_exp), width=np.full(n_exp, size, np.int32),
+                   height=np.full(n_exp, size, np.int32))
+    src = field_states(rng, n_src, lon)
+    snr = rng.uniform(*snr_range, n_src)
+    flux = flux_for_snr(snr / math.sqrt(n_exp), 1.55, 1.0)
+    art = field_states(rng, n_art, lon)
+    art_exp = rng.integers(0, n_exp, n_art)
+    art_flux = flux_for_snr(rng.uniform(*art_snr, n_art), 1.55, 1.0)
+    rand = field_states(rng, n_rand, lon)
+    return Sky(name="vetting", ex=ex, t0=t0, states=src, inj_states=src, inj_flux=flux,
+               inj_orbit=np.arange(n_src), seed=seed,
+               meta=dict(snr=snr, art_states=art, art_exp=art_exp, art_flux=art_flux,
+                         rand_states=rand))

@@ -1,0 +1,160 @@
+"""GPU parity of the learned vetting stage (stamps, CNN forward, loss gradient,
+Adam) against the FP64 oracle, and what the trained network gains over the
+plain SNR threshold at the same recall."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from oracle import vetting as V
+from paper_2503_08854_gb300 import ndt, synth, vetting
+
+from _gpu_helpers import Gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+def _sky():
+    sky = synth.grid_sky(n_exp=6, size=100, n_r=4, n_v=32, scale_arcsec=1.0, inj_snr=4.0,
+                         n_inj=3, seed=3)
+    imgs = synth.noise_images(sky.ex, sky.seed)
+    xy = O.predict(sky.inj_states, sky.t0, sky.ex)
+    synth.render_sources(imgs, xy, sky.inj_flux, sky.ex.sigma)
+    return sky, imgs
+
+
+def test_stamps_match_oracle(gpu):
+    sky, imgs = _sky()
+    gpu.load(sky.ex, imgs)
+    rng = np.random.default_rng(0)
+    cand = np.concatenate([sky.inj_orbit, rng.choice(len(sky.states), 40, replace=False), [-1]])
+    n = len(cand)
+    st = gpu.soa(sky.states)
+    cd = torch.as_tensor(cand, dtype=torch.int64, device=gpu.dev)
+    f32 = torch.empty((n, 2, 21, 21), device=gpu.dev)
+    bf = torch.empty((n, 2, 21, 21), dtype=torch.bfloat16, device=gpu.dev)
+    torch.cuda.synchronize()
+    ndt.stamps(gpu.ctx, st, sky.t0, len(sky.states), cd, f32, bf)
+    g = f32.cpu().numpy().astype(np.float64)
+    # BF16 output is the round-to-nearest-even of the FP32 stamp
+    assert torch.equal(bf.cpu(), f32.cpu().to(torch.bfloat16))
+    assert np.all(g[-1] == 0.0)                       # out-of-range candidate
+    planes = [O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j]) for j in range(sky.ex.n)]
+    xy = O.predict(sky.states[cand[:-1]], sky.t0, sky.ex)
+    ref = V.stamps(xy, planes, sky.ex.width, sky.ex.height)
+    amb = O.stack(sky.states[cand[:-1]], sky.t0, sky.ex, images=list(imgs))["n_amb"] > 0
+    ok = ~amb
+    assert ok.sum() >= n - 5
+    d0 = np.abs(g[:-1, 0][ok] - ref[ok, 0])
+    d1 = np.abs(g[:-1, 1][ok] - ref[ok, 1])
+    assert d0.max() <= 1e-5 * max(1.0, np.abs(ref[ok, 0]).max()), d0.max()
+    assert d1.max() <= 1e-4 * max(1.0, np.abs(ref[ok, 1]).max()), d1.max()
+    assert np.abs(ref[:, 0]).max() > 3.0                # the injected sources are in there
+
+
+def _bf16_batch(seed, n):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=(n, 2, 21, 21)).astype(np.float32)
+    x[:, 0, 8:13, 8:13] += 2.0
+    xb = torch.from_numpy(x).to(torch.bfloat16)
+    return xb, xb.to(torch.float64).numpy()
+
+
+def _params(seed):
+    th = V.init_params(seed)
+    th += np.random.default_rng(seed + 1).normal(scale=0.02, size=th.shape)
+    return th
+
+
+def test_cnn_forward_matches_oracle(gpu):
+    xb, x64 = _bf16_batch(1, 37)
+    th = _params(2)
+    p = torch.as_tensor(th, dtype=torch.float32, device=gpu.dev)
+    ref = V.forward(th.astype(np.float32).astype(np.float64), x64)
+    z = vetting.logits(gpu.ctx, p, xb.to(gpu.dev))
+    np.testing.assert_allclose(z.cpu().numpy(), ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+
+
+def test_cnn_gradient_matches_oracle(gpu):
+    """Gradients of the mean BCE agree with the FP64 oracle to 1e-3 relative per
+    parameter block (the oracle's own gradient is pinned by finite differences)."""
+    xb, x64 = _bf16_batch(3, 48)
+    th = _params(4).astype(np.float32).astype(np.float64)
+    y = (np.arange(48) % 3 == 0).astype(np.float64)
+    loss_ref, g_ref = V.loss_and_grad(th, x64, y)
+    p = torch.as_tensor(th, dtype=torch.float32, device=gpu.dev)
+    grad = torch.empty_like(p)
+    yl = torch.as_tensor(y, dtype=torch.float32, device=gpu.dev)
+    torch.cuda.synchronize()
+    loss = ndt.cnn_loss_grad(gpu.ctx, p, xb.to(gpu.dev), yl, 48, grad)
+    assert loss == pytest.approx(loss_ref, rel=1e-5)
+    g = grad.cpu().numpy().astype(np.float64)
+    off = 0
+    for name, shp in V.SHAPES:
+        k = int(np.prod(shp))
+        a, b = g[off:off + k], g_ref[off:off + k]
+        rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-12)
+        assert rel <= 1e-3, (name, rel)
+        off += k
+
+
+def test_adam_step(gpu):
+    rng = np.random.default_rng(5)
+    n = V.N_PARAMS
+    th = rng.normal(size=n).astype(np.float32)
+    grads = [rng.normal(size=n).astype(np.float32) for _ in range(3)]
+    p = torch.as_tensor(th, device=gpu.dev)
+    m = torch.zeros_like(p)
+    v = torch.zeros_like(p)
+    ref_p, ref_m, ref_v = th.astype(np.float64), np.zeros(n), np.zeros(n)
+    for t, gr in enumerate(grads, start=1):
+        g = torch.as_tensor(gr, device=gpu.dev)
+        ndt.cnn_adam_step(gpu.ctx, p, g, m, v, t, lr=1e-2)
+        ref_m = 0.9 * ref_m + 0.1 * gr
+        ref_v = 0.999 * ref_v + 0.001 * gr.astype(np.float64) ** 2
+        ref_p -= 1e-2 * (ref_m / (1 - 0.9 ** t)) / (np.sqrt(ref_v / (1 - 0.999 ** t)) + 1e-8)
+    ndt.synchronize(gpu.ctx)
+    np.testing.assert_allclose(p.cpu().numpy(), ref_p, rtol=1e-5, atol=1e-6)
+
+
+def test_vet_entry_point_scores_its_stamps(gpu):
+    sky, imgs = _sky()
+    gpu.load(sky.ex, imgs)
+    cand = torch.as_tensor(np.arange(0, len(sky.states), 97), dtype=torch.int64, device=gpu.dev)
+    n = cand.numel()
+    st = gpu.soa(sky.states)
+    p = vetting.init_params(7, gpu.dev)
+    scores = torch.empty(n, device=gpu.dev)
+    bf = torch.empty((n, 2, 21, 21), dtype=torch.bfloat16, device=gpu.dev)
+    torch.cuda.synchronize()
+    ndt.vet(gpu.ctx, p, st, sky.t0, len(sky.states), cand, scores)
+    ndt.stamps(gpu.ctx, st, sky.t0, len(sky.states), cand, None, bf)
+    z = vetting.logits(gpu.ctx, p, bf)
+    np.testing.assert_allclose(scores.cpu().numpy(), torch.sigmoid(z).cpu().numpy(), rtol=1e-6, atol=1e-7)
+
+
+def test_trained_vetter_beats_snr_threshold(gpu):
+    """Trained on the pipeline's own injected asteroids against random orbits,
+    single-exposure artefacts and noise peaks, the network keeps 90 % of the
+    held-out asteroids at a lower false-positive rate than the stacked-SNR
+    threshold does at the same recall."""
+    x, y, kind, snr = vetting.make_set(gpu.ctx, 11, gpu.dev, n_sky=6)
+    xt, yt, kt, st = vetting.make_set(gpu.ctx, 12, gpu.dev, n_sky=2)
+    p = vetting.init_params(0, gpu.dev)
+    losses = vetting.train(gpu.ctx, p, x, y, epochs=6, batch=256, lr=2e-3)
+    assert np.mean(losses[-5:]) < 0.6 * np.mean(losses[:5])
+    z = vetting.logits(gpu.ctx, p, xt).cpu().numpy()
+    pos = kt == 0
+    fpr_cnn, _ = vetting.fpr_at_recall(z[pos], z[~pos], 0.9)
+    fpr_snr, _ = vetting.fpr_at_recall(st[pos], st[~pos], 0.9)
+    print(f"FPR at 90% recall: CNN {fpr_cnn:.3f} vs SNR threshold {fpr_snr:.3f}")
+    assert fpr_cnn < 0.75 * fpr_snr
