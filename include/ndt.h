@@ -250,6 +250,33 @@ ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, flo
 ndt_status ndt_vet(ndt_ctx *ctx, const float *params, const double *states, double t0,
                    int64_t n_orbits, const int64_t *cand_idx, int64_t n_cand, float *scores);
 
+/*
+ * topk_noalloc: the ranking of ndt_topk_candidates (k largest values, ties to
+ * the lower index, NaN ranked with -inf) for callers that cannot let a
+ * library allocate device memory, for example a host framework that keeps
+ * nearly all of the GPU's memory in its own pool, or a real-time loop that
+ * cannot pay for cudaMalloc/cudaFree between frames.  It allocates nothing:
+ * its scratch is one array of 200 KB compiled into the library, held on
+ * every GPU that loads the library until the process exits.  The paper has
+ * no counterpart; this is an interface convenience.
+ *   snr_dev   n FP32 values in device memory (e.g. the snr output of
+ *             ndt_stack_orbits).
+ *   n, k      1 <= n <= 67,108,864 and 1 <= k <= 8192 (k is clamped to n);
+ *             anything larger returns NDT_EINVAL.
+ *   idx_out   k int64 indices, snr_out k FP32 values, device memory of the
+ *             same device (either may be NULL).
+ *   cuda_stream  the cudaStream_t the kernels are issued on (NULL = the
+ *             legacy default stream); the call returns without waiting.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device made current); make that first call before any
+ * stream capture begins.  Every call on a device shares the one array and the
+ * next call overwrites it: calls whose kernels overlap on the GPU (different
+ * streams or host threads) race and must be serialised by the caller.  Host
+ * pointers return NDT_EINVAL; a CUDA error returns NDT_ECUDA.
+ */
+ndt_status ndt_topk_noalloc(const float *snr_dev, int64_t n, int64_t k, int64_t *idx_out,
+                            float *snr_out, void *cuda_stream);
+
 /* Copy the context's counters into *out. */
 ndt_status ndt_get_stats(ndt_ctx *ctx, ndt_stats *out);
 

@@ -71,6 +71,7 @@ _lib.ndt_cnn_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i32, C.c_floa
                                    C.c_float, C.c_float]
 _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
+_lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
 
 
 class NdtError(RuntimeError):
@@ -245,10 +246,21 @@ def vet(ctx, params, states_soa, t0, n_orbits, cand_idx, scores):
                              _ptr(cand_idx), int(len(cand_idx)), _ptr(scores)))
 
 
+def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
+    """ndt_topk_noalloc: top-k of a device array with the library's fixed
+    scratch (no device allocation); device pointers only, asynchronous on
+    ``stream`` (a torch.cuda.Stream, a raw cudaStream_t, or None)."""
+    raw = getattr(stream, "cuda_stream", stream)
+    st = _lib.ndt_topk_noalloc(_ptr(snr), int(n), int(k), _ptr(idx_out), _ptr(snr_out), raw)
+    if st != OK:
+        raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
+
+
 def exported_symbols():
     """Names of the C entry points this binding uses (all must be exported)."""
     return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
             "ndt_load_exposures", "ndt_stack_orbits", "ndt_topk_candidates",
             "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
-            "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet"]
+            "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
+            "ndt_topk_noalloc"]
