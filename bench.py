@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--tiles", default=None, help="fixed OT,ET for the persistent form (no autotune)")
+    p.add_argument("--no-vet", action="store_true", help="skip the CNN vetting stage")
+    p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
     return p.parse_args()
 
 
@@ -157,25 +159,66 @@ class Form:
         self.name, self.plane, self.mode, self.graph = name, plane, mode, graph
 
 
-def run_steps(ctx, stream, sky, imgs, states, k, n_steps, idx_out, snr_out, plane):
+def run_steps(ctx, stream, sky, imgs, states, k, n_steps, idx_out, snr_out, plane, vet=None):
     """Device-resident steps; per-step device time from CUDA events on the
-    library's stream, plus the stack kernel's own event time."""
+    library's stream, plus the stack kernel's own event time.  With ``vet``
+    (params, scores) the top-k candidates are also vetted by the CNN."""
     import torch
     from paper_2503_08854_gb300 import ndt
     n = states.shape[1]
-    step_ms, stack_ms = [], []
+    step_ms, stack_ms, vet_ms = [], [], []
     for _ in range(n_steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=plane)
         ndt.stack_orbits(ctx, states, sky.t0, n)
         ndt.topk_candidates(ctx, k, idx_out, snr_out)
+        e2.record(stream)
+        if vet is not None:
+            ndt.vet(ctx, vet[0], states, sky.t0, n, idx_out, vet[1])
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+        vet_ms.append(e2.elapsed_time(e1))
         stack_ms.append(ndt.get_stats(ctx)["last_stack_ms"])
-    return step_ms, stack_ms
+    return step_ms, stack_ms, vet_ms
+
+
+def train_vetter(device, seed=5, n_train_sky=12, n_test_sky=3):
+    """Untimed setup: synthesise vetting stamps with the library (injected
+    asteroids vs random orbits, single-exposure artefacts and noise peaks),
+    train the CNN with the library's forward/backward/Adam kernels, and
+    measure the false-positive rate at 90 % recall on held-out skies against
+    the stacked-SNR threshold."""
+    import torch
+    from paper_2503_08854_gb300 import ndt, vetting
+    stream = torch.cuda.Stream(device=device)
+    ctx = ndt.create(device.index, stream)
+    try:
+        t = time.perf_counter()
+        x, y, kind, _ = vetting.make_set(ctx, seed, device, n_sky=n_train_sky)
+        xt, yt, kt, st = vetting.make_set(ctx, seed + 1, device, n_sky=n_test_sky)
+        t_data = time.perf_counter() - t
+        p = vetting.init_params(seed, device)
+        t = time.perf_counter()
+        losses = vetting.train(ctx, p, x, y, epochs=6, batch=256, lr=2e-3)
+        t_train = time.perf_counter() - t
+        z = vetting.logits(ctx, p, xt).cpu().numpy()
+    finally:
+        ndt.destroy(ctx)
+    pos = kt == 0
+    fpr_cnn, _ = vetting.fpr_at_recall(z[pos], z[~pos], 0.9)
+    fpr_snr, _ = vetting.fpr_at_recall(st[pos], st[~pos], 0.9)
+    info = {"train_stamps": int(x.shape[0]), "test_stamps": int(xt.shape[0]),
+            "train_steps": len(losses), "train_s": round(t_train, 2), "data_s": round(t_data, 2),
+            "final_loss": float(np.mean(losses[-5:])),
+            "fpr_at_90pct_recall": {"cnn": fpr_cnn, "snr_threshold": fpr_snr},
+            "workload": "vetting skies: 10 exposures 1024^2, 400 injected asteroids (stacked "
+                        "SNR 3-10), 400 random orbits, 400 one-exposure artefacts, 400 noise "
+                        "peaks of 20,000 orbits on a source-free sky, per sky"}
+    return p, info
 
 
 RECALL_SNR = 6.0   # detection threshold on the stacked SNR for recall
@@ -198,7 +241,7 @@ def recall_at_threshold(snr, sky, thr=RECALL_SNR):
     return float((best >= thr).float().mean().item())
 
 
-def bench_form(args, form, sky, stream, imgs, states, device, barrier):
+def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_params=None):
     import torch
     from paper_2503_08854_gb300 import ndt
     n = states.shape[1]
@@ -221,13 +264,16 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier):
                 tiles = {"orbit_tile": ot, "exp_tile": et,
                          "sweep_ms": [round(float(t), 2) for t in times]}
             ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, ot, et, use_graph=form.graph)
-        run_steps(ctx, stream, sky, imgs, states, k, args.warmup, idx, val, form.plane)
+        vet = None
+        if vet_params is not None and form.name == "chosen":
+            vet = (vet_params, torch.empty(k, device=device))
+        run_steps(ctx, stream, sky, imgs, states, k, args.warmup, idx, val, form.plane, vet)
         launches0 = ndt.get_stats(ctx)["kernel_launches"]
         barrier()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
-        step_ms, stack_ms = run_steps(ctx, stream, sky, imgs, states, k, args.steps, idx, val,
-                                      form.plane)
+        step_ms, stack_ms, vet_ms = run_steps(ctx, stream, sky, imgs, states, k, args.steps, idx,
+                                              val, form.plane, vet)
         torch.cuda.synchronize(device)
         wall = time.perf_counter() - t0
         stats = ndt.get_stats(ctx)
@@ -237,7 +283,8 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier):
         ndt.stack_orbits(ctx, states, sky.t0, n, snr=snr_all)
         ndt.synchronize(ctx)
         rec_thr = recall_at_threshold(snr_all, sky)
-        out = dict(step_ms=step_ms, stack_ms=stack_ms, wall_s=wall, launches=launches,
+        out = dict(step_ms=step_ms, stack_ms=stack_ms, vet_ms=vet_ms if vet else None,
+                   wall_s=wall, launches=launches,
                    valid=stats["valid_samples"], samples=stats["samples"], recall=rec_thr,
                    recall_topk=rec,
                    planes_ms=stats["last_planes_ms"], topk_ms=stats["last_topk_ms"], tiles=tiles,
@@ -380,6 +427,10 @@ def main():
     from paper_2503_08854_gb300 import __name__ as _pkg  # noqa: F401
     import __graft_entry__
     __graft_entry__.build()
+    vet_params, vet_info = None, None
+    if "chosen" in args.forms.split(",") and not args.no_vet:
+        vet_params, vet_info = train_vetter(device, n_train_sky=args.vet_skies,
+                                            n_test_sky=max(1, args.vet_skies // 4))
     sky, stream, imgs, states = make_workload(args, rank, device)
     forms = {"plain": Form("plain", "f32", "plain", False),
              "chosen": Form("chosen", args.plane, "persistent", True)}
@@ -387,7 +438,8 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     for name in args.forms.split(","):
-        res, e = bench_form(args, forms[name], sky, stream, imgs, states, device, barrier)
+        res, e = bench_form(args, forms[name], sky, stream, imgs, states, device, barrier,
+                            vet_params)
         results[name] = res
         if e is not None:
             e2e = e
@@ -415,6 +467,11 @@ def main():
         "gpu_launches": int(r["launches"]),
         "clocks": clk,
     }
+    if vet_info is not None and r.get("vet_ms"):
+        vet_info["vet_ms_per_step"] = statistics.mean(r["vet_ms"])
+        vet_info["vetted_candidates_per_s"] = min(args.k, states.shape[1]) / (
+            statistics.mean(r["vet_ms"]) / 1e3)
+        line["vetting"] = vet_info
     for name, res in results.items():
         s = statistics.mean(res["step_ms"]) / 1e3
         line[name] = {"samples_per_s": res["samples"] / s, "ms_per_step": s * 1e3,

@@ -59,7 +59,7 @@ struct ndt_ctx {
   std::vector<int32_t> sorted_to_table, table_to_sorted;
   std::vector<ExpDev> ex_host;
   int plane_type = kF32;
-  DevBuf ex_dev, pos_to_table_dev, planes, planes_tmp, jobs_dev, absmax_dev, scales_dev;
+  DevBuf ex_dev, pos_to_table_dev, planes, jobs_dev, absmax_dev;
   DevBuf stage_images, stage_vars;
   // orbit batch
   DevBuf stage_states, snr, out_tmp, xy_tmp;
@@ -221,8 +221,8 @@ void ndt_destroy(ndt_ctx* c) {
   if (c->graph) cudaGraphExecDestroy(c->graph);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
-  DevBuf* bufs[] = {&c->ex_dev, &c->pos_to_table_dev, &c->planes, &c->planes_tmp, &c->jobs_dev,
-                    &c->absmax_dev, &c->scales_dev, &c->stage_images, &c->stage_vars,
+  DevBuf* bufs[] = {&c->ex_dev, &c->pos_to_table_dev, &c->planes, &c->jobs_dev,
+                    &c->absmax_dev, &c->stage_images, &c->stage_vars,
                     &c->stage_states, &c->snr, &c->out_tmp, &c->xy_tmp, &c->fam_orb_off,
                     &c->fam_exp_off, &c->fam_exp_pos, &c->item_off, &c->fam_order,
                     &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
@@ -303,6 +303,18 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     PlaneJob& J = jobs[s];
     J.var_c = m.variance > 0.0f ? m.variance : 1.0f;
     J.sigma = m.psf_sigma_px;
+    // unit-sum 1-D Gaussian window of the truncated PSF (FP64, rounded once)
+    J.R = (int)std::ceil(4.0 * (double)m.psf_sigma_px);
+    {
+      double w[2 * kMaxPsfRadius + 1], sum = 0.0;
+      const double s2 = 2.0 * (double)m.psf_sigma_px * (double)m.psf_sigma_px;
+      for (int k = -J.R; k <= J.R; ++k) sum += (w[k + J.R] = std::exp(-(double)(k * k) / s2));
+      for (int k = 0; k <= 2 * J.R; ++k) {
+        const double g = w[k] / sum;
+        J.g[k] = (float)g;
+        J.g2[k] = (float)(g * g);
+      }
+    }
     J.W = m.width;
     J.H = m.height;
     J.tiles_x = e.tiles_x;
@@ -346,40 +358,42 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
   NDT_CK(ctx->jobs_dev.ensure(sizeof(PlaneJob) * n_exp), "job table");
   NDT_CK(cudaMemcpyAsync(ctx->jobs_dev.p, jobs.data(), sizeof(PlaneJob) * n_exp,
                          cudaMemcpyHostToDevice, ctx->stream), "job upload");
+  int max_R = 0;
+  for (const PlaneJob& J : jobs) max_R = std::max(max_R, J.R);
+  const bool any_var = variances != nullptr;
   const size_t pair_bytes = plane_dtype == NDT_PLANE_F32 ? 8 : 4;
   NDT_CK(ctx->planes.ensure(pair_bytes * plane_elems), "plane allocation");
-  float2* f32 = nullptr;
-  if (plane_dtype == NDT_PLANE_F32) {
-    f32 = ctx->planes.as<float2>();
-  } else {
-    NDT_CK(ctx->planes_tmp.ensure(8 * plane_elems), "FP32 plane scratch");
-    f32 = ctx->planes_tmp.as<float2>();
-  }
   record(ctx, 0);
-  NDT_CK(launch_planes_f32(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, f32, ctx->stream),
-         "plane kernel");
-  ctx->launches += 1;
-  if (plane_dtype != NDT_PLANE_F32) {
+  if (plane_dtype == NDT_PLANE_F32) {
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneStoreF32,
+                         ctx->planes.p, nullptr, ctx->stream), "plane kernel");
+    ctx->launches += 1;
+  } else {
+    // pass 1: largest |psi| and phi per plane (nothing stored); pass 2: the
+    // same planes again, written as 16-bit pairs scaled by those maxima
     NDT_CK(ctx->absmax_dev.ensure(8 * n_exp), "absmax");
-    NDT_CK(ctx->scales_dev.ensure(8 * n_exp), "scales");
     NDT_CK(cudaMemsetAsync(ctx->absmax_dev.p, 0, 8 * n_exp, ctx->stream), "memset");
-    NDT_CK(launch_plane_absmax(ctx->jobs_dev.as<PlaneJob>(), n_exp, f32,
-                               ctx->absmax_dev.as<unsigned int>(), ctx->stream), "absmax kernel");
-    NDT_CK(launch_plane_quantize(ctx->jobs_dev.as<PlaneJob>(), n_exp, f32,
-                                 ctx->absmax_dev.as<unsigned int>(), plane_dtype, ctx->planes.p,
-                                 ctx->scales_dev.as<float>(), ctx->stream), "quantize kernel");
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneAbsMax, nullptr,
+                         ctx->absmax_dev.as<unsigned int>(), ctx->stream), "plane max kernel");
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var,
+                         plane_dtype == NDT_PLANE_BF16 ? kPlaneStoreBF16 : kPlaneStoreF16,
+                         ctx->planes.p, ctx->absmax_dev.as<unsigned int>(), ctx->stream),
+           "plane kernel");
     ctx->launches += 2;
   }
   record(ctx, 1);
   ctx->have_planes_ev = true;
   if (plane_dtype != NDT_PLANE_F32) {
-    std::vector<float> sc(2 * n_exp);
-    NDT_CK(cudaMemcpyAsync(sc.data(), ctx->scales_dev.p, 8 * n_exp, cudaMemcpyDeviceToHost,
+    std::vector<unsigned int> mx(2 * n_exp);
+    NDT_CK(cudaMemcpyAsync(mx.data(), ctx->absmax_dev.p, 8 * n_exp, cudaMemcpyDeviceToHost,
                            ctx->stream), "scale read-back");
     NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
-    for (int s = 0; s < n_exp; ++s) {
-      ctx->ex_host[s].s_psi = sc[2 * s];
-      ctx->ex_host[s].s_phi = sc[2 * s + 1];
+    for (int s = 0; s < n_exp; ++s) {   // the kernel's scales: max / 2^14, or 1 for an empty plane
+      float a0, a1;
+      std::memcpy(&a0, &mx[2 * s], 4);
+      std::memcpy(&a1, &mx[2 * s + 1], 4);
+      ctx->ex_host[s].s_psi = a0 > 0.0f ? a0 / 16384.0f : 1.0f;
+      ctx->ex_host[s].s_phi = a1 > 0.0f ? a1 / 16384.0f : 1.0f;
     }
   }
   NDT_CK(ctx->ex_dev.ensure(sizeof(ExpDev) * n_exp), "exposure table");

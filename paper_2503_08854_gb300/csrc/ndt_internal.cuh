@@ -327,16 +327,19 @@ struct PlaneJob {
   float var_c;
   float sigma;
   int32_t W, H, tiles_x, tiles_y;
-  int64_t plane_off;    // element offset in the FP32 plane buffer
+  int64_t plane_off;    // element offset in the plane buffer
+  int32_t R;            // window radius ceil(4 sigma)
+  int32_t pad_;
+  float g[2 * kMaxPsfRadius + 1];    // unit-sum 1-D Gaussian window (host FP64, rounded)
+  float g2[2 * kMaxPsfRadius + 1];   // its square
 };
 
-cudaError_t launch_planes_f32(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, float2* out,
-                              cudaStream_t st);
-cudaError_t launch_plane_absmax(const PlaneJob* jobs_dev, int n_jobs, const float2* planes,
-                                unsigned int* absmax2, cudaStream_t st);
-cudaError_t launch_plane_quantize(const PlaneJob* jobs_dev, int n_jobs, const float2* planes,
-                                  const unsigned int* absmax2, int plane_type, void* out,
-                                  float* scales2, cudaStream_t st);
+// Plane kernel outputs: FP32 pairs, or (two passes) the largest |psi| and phi
+// of each plane, then BF16/FP16 pairs scaled by those maxima.
+enum PlaneMode : int32_t { kPlaneStoreF32 = 0, kPlaneAbsMax = 1, kPlaneStoreBF16 = 2, kPlaneStoreF16 = 3 };
+
+cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
+                          int mode, void* out, unsigned int* absmax2, cudaStream_t st);
 cudaError_t launch_plane_decode(const void* planes, int plane_type, const ExpDev* e_host_copy,
                                 float* psi, float* phi, cudaStream_t st);
 

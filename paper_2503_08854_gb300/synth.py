@@ -384,3 +384,56 @@ def vetting_sky(*, seed, n_exp=10, nights=20.0, size=1024, scale_arcsec=2.0, n_s
                inj_orbit=np.arange(n_src), seed=seed,
                meta=dict(snr=snr, art_states=art, art_exp=art_exp, art_flux=art_flux,
                          rand_states=rand))
+
+
+# --------------------------------------------------------------------------
+# Batched uneven workload (orbit families with uneven exposure coverage)
+# --------------------------------------------------------------------------
+
+def batched_sky(*, n_fam=4096, fam_size=16384, n_exp=400, size=2048, days=365.0, seed=4,
+                scale_arcsec=60.0, lon=1.2, fam_exp_range=(20, 400)) -> Sky:
+    """Orbit families mixing near-Earth (q < 1.3 AU), main-belt and Kuiper-belt
+    (30-50 AU) hypotheses, each a seed state near opposition at the mid-year
+    epoch t0 plus seeded state jitter; each family is tested against a random
+    subset of U[fam_exp_range] of the exposures (the CSR lists).  Exposures:
+    pairs 30 min apart on n_exp/2 random nights of a year; pointings follow the
+    anti-solar direction (a circular reference body just outside the observer's
+    orbit) with a wide field."""
+    rng = np.random.default_rng(seed)
+    nights = np.sort(rng.choice(int(days), n_exp // 2, replace=False)).astype(np.float64)
+    mjd = np.sort(np.concatenate([60000.3 + nights, 60000.3 + nights + 30.0 / 1440.0]))[:n_exp]
+    t0 = float(60000.0 + days / 2.0)
+    obs = observer_position(mjd, t0, lon)
+    crval = tracking_pointings(mjd, obs, t0, 1.0001, lon)
+    s = scale_arcsec / 3600.0
+    sigma = rng.uniform(1.2, 2.0, n_exp).astype(np.float32).astype(np.float64)
+    ex = Exposures(mjd=mjd, obs=obs, crval=crval,
+                   crpix=np.tile(np.array([size / 2.0, size / 2.0]), (n_exp, 1)),
+                   cd=np.tile(np.array([[-s, 0.0], [0.0, s]]), (n_exp, 1, 1)), sigma=sigma,
+                   var=np.ones(n_exp), width=np.full(n_exp, size, np.int32),
+                   height=np.full(n_exp, size, np.int32))
+    kind = rng.integers(0, 3, n_fam)                         # 0 NEO, 1 MBA, 2 KBO
+    a = np.where(kind == 0, rng.uniform(1.0, 2.0, n_fam),
+                 np.where(kind == 1, rng.uniform(2.1, 3.3, n_fam), rng.uniform(30.0, 50.0, n_fam)))
+    e_max = np.where(kind == 0, 0.6, 0.2)
+    e = rng.uniform(0.0, 1.0, n_fam) * e_max
+    e = np.where(kind == 0, np.maximum(e, 1.0 - 1.3 / a + 1e-3), e)   # q < 1.3 AU
+    inc = np.radians(rng.uniform(0.0, 15.0, n_fam))
+    u = rng.uniform(-0.05, 0.05, n_fam)
+    lam = lon + rng.uniform(-0.05, 0.05, n_fam)
+    node = lam - np.arctan2(np.cos(inc) * np.sin(u), np.cos(u))
+    argp = rng.uniform(0.0, 2 * math.pi, n_fam)
+    seeds = state_from_elements(a, e, inc, node, argp, u - argp)
+    states = np.repeat(seeds, fam_size, axis=0)
+    r = np.linalg.norm(seeds[:, :3], axis=1).repeat(fam_size)
+    jit = np.concatenate([rng.normal(0.0, 1.0, (len(states), 3)) * (1e-4 * r)[:, None],
+                          rng.normal(0.0, 1.0, (len(states), 3)) * (2e-6 / np.sqrt(r))[:, None]], 1)
+    jit[::fam_size] = 0.0
+    states += jit
+    fo = (np.arange(n_fam + 1) * fam_size).astype(np.int64)
+    counts = rng.integers(fam_exp_range[0], fam_exp_range[1] + 1, n_fam)
+    fe = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    fi = np.concatenate([rng.choice(n_exp, c, replace=False) for c in counts]).astype(np.int32)
+    return Sky(name="batched", ex=ex, t0=t0, states=states, inj_states=seeds,
+               inj_flux=np.zeros(n_fam), inj_orbit=fo[:-1].copy(), seed=seed,
+               families=(fo, fe, fi), meta=dict(kind=kind, fam_size=fam_size))

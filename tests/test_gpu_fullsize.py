@@ -1,0 +1,135 @@
+"""Parity at full workload sizes, in the launch forms the benchmark times:
+every orbit is stacked on the GPU, a random sample of orbits is recomputed by
+the oracle (planes evaluated at the gathered pixels from the same images),
+and the precision variant is reported against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2503_08854_gb300 import ndt, synth
+
+from _gpu_helpers import Gpu, POS_TOL, check_stack
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture
+def gpu():
+    g = Gpu()
+    yield g
+    g.close()
+
+
+def _device_sky(gpu, sky):
+    """Noise drawn on the device, sources rendered at oracle positions."""
+    imgs = synth.noise_images_torch(sky.ex, sky.seed, gpu.dev)
+    if np.any(sky.inj_flux > 0):
+        xy = O.predict(sky.inj_states, sky.t0, sky.ex, nthreads=0)
+        synth.render_sources_torch(imgs, xy, sky.inj_flux, sky.ex.sigma)
+    torch.cuda.synchronize()
+    return imgs
+
+
+def _stack_all(gpu, sky, imgs, plane, mode, families=None):
+    ndt.load_exposures(gpu.ctx, sky.ex, imgs, plane_dtype=plane)
+    if mode == "persistent":
+        ndt.set_launch(gpu.ctx, ndt.LAUNCH_PERSISTENT, 64, 16, use_graph=True)
+    else:
+        ndt.set_launch(gpu.ctx, ndt.LAUNCH_PLAIN)
+    n = len(sky.states)
+    st = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(gpu.dev)
+    out = dict(psi=torch.empty(n, device=gpu.dev), phi=torch.empty(n, device=gpu.dev),
+               nobs=torch.empty(n, dtype=torch.int32, device=gpu.dev),
+               snr=torch.empty(n, device=gpu.dev))
+    fam = None
+    if families is not None:
+        fam = tuple(torch.from_numpy(np.ascontiguousarray(x)).to(gpu.dev) for x in families)
+    torch.cuda.synchronize()
+    ndt.stack_orbits(gpu.ctx, st, sky.t0, n, families=fam, psi_sum=out["psi"], phi_sum=out["phi"],
+                     nobs=out["nobs"], snr=out["snr"])
+    ndt.synchronize(gpu.ctx)
+    assert gpu.stats()["kepler_failures"] == 0
+    return out
+
+
+def _sampled(out, sel):
+    return {k: v[torch.as_tensor(sel, device=v.device)].cpu().numpy() for k, v in out.items()}
+
+
+@pytest.mark.parametrize("form", [("f32", "plain"), ("bf16", "persistent")])
+def test_mba_full_size_sampled(gpu, form):
+    """200 exposures of 4096^2, 16.4 M orbits, as the benchmark runs it."""
+    plane, mode = form
+    sky = synth.mba_sky()
+    imgs = _device_sky(gpu, sky)
+    out = _stack_all(gpu, sky, imgs, plane, mode)
+    sel = np.sort(np.random.default_rng(1).choice(len(sky.states), 256, replace=False))
+    sel = np.concatenate([sky.inj_orbit[:16], sel])
+    host = imgs.cpu().numpy()
+    ref = O.stack(sky.states[sel], sky.t0, sky.ex, images=[host[j] for j in range(sky.ex.n)])
+    g = _sampled(out, sel)
+    if plane == "f32":
+        check_stack(g, ref)
+    else:
+        nu = O.snr(ref["Psi"], ref["Phi"], ref["nobs"])
+        ok = (ref["n_amb"] == 0) & np.isfinite(nu)
+        assert np.array_equal(g["nobs"][ref["n_amb"] == 0], ref["nobs"][ref["n_amb"] == 0])
+        err = np.abs(g["snr"][ok] - nu[ok]) / np.maximum(1.0, np.abs(nu[ok]))
+        assert err.max() <= 2.0 ** -7, err.max()
+    # positions of the sampled orbits through the same device code
+    xy = torch.empty(len(sel) * sky.ex.n * 2, dtype=torch.float64, device=gpu.dev)
+    st = torch.from_numpy(np.ascontiguousarray(sky.states[sel].T)).to(gpu.dev)
+    torch.cuda.synchronize()
+    ndt.predict_positions(gpu.ctx, st, sky.t0, len(sel), xy)
+    xy = xy.cpu().numpy().reshape(len(sel), sky.ex.n, 2)
+    rx = O.predict(sky.states[sel], sky.t0, sky.ex)
+    fin = np.isfinite(rx)
+    assert np.abs(xy[fin] - rx[fin]).max() <= POS_TOL
+
+
+def test_batched_uneven_full_size_sampled(gpu):
+    """4,096 families x 16,384 orbits (NEO, MBA, KBO), 20-400 of 400 exposures
+    of 2048^2 each, FP32 planes, persistent work queue under a CUDA graph."""
+    sky = synth.batched_sky()
+    imgs = _device_sky(gpu, sky)
+    out = _stack_all(gpu, sky, imgs, "f32", "persistent", families=sky.families)
+    fo, fe, fi = sky.families
+    rng = np.random.default_rng(2)
+    sel = np.sort(rng.choice(len(sky.states), 256, replace=False))
+    fam_of = np.searchsorted(fo, sel, side="right") - 1
+    lists = [fi[fe[f]:fe[f + 1]] for f in fam_of]
+    mfo = np.arange(len(sel) + 1, dtype=np.int64)
+    mfe = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(np.int64)
+    host = imgs.cpu().numpy()
+    ref = O.stack(sky.states[sel], sky.t0, sky.ex, images=[host[j] for j in range(sky.ex.n)],
+                  families=(mfo, mfe, np.concatenate(lists)))
+    check_stack(_sampled(out, sel), ref)
+    assert gpu.stats()["samples"] == int(np.sum((fo[1:] - fo[:-1]) * (fe[1:] - fe[:-1])))
+
+
+def test_precision_variant_report(gpu, capsys):
+    """The tiny workload refined to 102,400 orbits: BF16/FP16 planes against the
+    FP64 oracle (SNR error) and recall of the injected sources against FP32."""
+    sky = synth.grid_sky(n_r=25)
+    imgs = synth.noise_images(sky.ex, sky.seed)
+    xy = O.predict(sky.inj_states, sky.t0, sky.ex)
+    synth.render_sources(imgs, xy, sky.inj_flux, sky.ex.sigma)
+    pl = [O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j]) for j in range(sky.ex.n)]
+    ref = O.stack(sky.states, sky.t0, sky.ex, planes=([p[0] for p in pl], [p[1] for p in pl]))
+    nu = O.snr(ref["Psi"], ref["Phi"], ref["nobs"])
+    ok = (ref["n_amb"] == 0) & np.isfinite(nu)
+    report = {}
+    for plane in ("f32", "bf16", "f16"):
+        gpu.load(sky.ex, imgs, plane=plane)
+        out = gpu.stack(sky.states, sky.t0)
+        idx, _ = gpu.topk(100)
+        err = np.abs(out["snr"][ok] - nu[ok]) / np.maximum(1.0, np.abs(nu[ok]))
+        recall = np.isin(sky.inj_orbit, idx).mean()
+        report[plane] = (float(err.max()), float(np.median(err)), float(recall))
+    with capsys.disabled():
+        for k, (mx, md, rc) in report.items():
+            print(f"\nprecision {k}: max SNR err {mx:.2e}, median {md:.2e}, recall {rc:.2f}")
+    assert report["f32"][0] <= 1e-5
+    assert report["bf16"][0] <= 2.0 ** -7 and report["f16"][0] <= 2.0 ** -10
+    assert report["bf16"][2] == report["f32"][2] and report["f16"][2] == report["f32"][2]
