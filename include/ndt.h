@@ -162,8 +162,9 @@ ndt_status ndt_stack_orbits(ndt_ctx *ctx, const double *states, double t0, int64
 /*
  * topk_candidates: the k orbits of the last stack with the largest nu,
  * sorted by nu descending and orbit index ascending (paper Algorithm 1,
- * FindSignificantResults).  k is clamped to the number of orbits; the
- * number written is returned in *k_out (may be NULL).  idx_out (int64) and
+ * FindSignificantResults).  k is clamped to the number of orbits (any k up
+ * to the batch size is supported); the number written is returned in *k_out
+ * (may be NULL).  idx_out (int64) and
  * snr_out (FP32) hold k entries each; either may be NULL.
  */
 ndt_status ndt_topk_candidates(ndt_ctx *ctx, int64_t k, int64_t *idx_out, float *snr_out,

@@ -628,7 +628,6 @@ ndt_status ndt_topk_candidates(ndt_ctx* ctx, int64_t k, int64_t* idx_out, float*
   if (k > n) k = n;
   if (k_out) *k_out = k;
   if (k == 0) return NDT_OK;
-  if (k > 8192) return fail(ctx, NDT_EINVAL, "k = %lld above the supported 8192", (long long)k);
   const size_t sb = topk_scratch_bytes(n, k);
   NDT_CK(ctx->topk_scratch.ensure(sb), "top-k scratch");
   const bool h_idx = idx_out && !is_device_ptr(idx_out), h_snr = snr_out && !is_device_ptr(snr_out);

@@ -7,8 +7,11 @@
 // finds the k-th key T, the number of keys below it and how many keys equal
 // to T are needed.  An order-preserving compaction then writes the keys
 // below T in index order followed by the lowest-index keys equal to T, and a
-// final sort of the k (key, index) pairs gives the ranking.  Every kernel is
-// a bounded pass; nothing waits on another block.
+// final sort of the k (key, index) pairs gives the ranking: a single-CTA
+// bitonic sort for k <= 8192, a stable multi-block LSD radix sort above.
+// Every kernel is a bounded pass; nothing waits on another block.
+#include <algorithm>
+
 #include "ndt_internal.cuh"
 
 namespace ndt {
@@ -228,6 +231,98 @@ __global__ void __launch_bounds__(1024) k_sort_small(const unsigned long long* _
   }
 }
 
+// ---------------------------------------------------------------------------
+// Large k: stable least-significant-digit radix sort of the k compacted items
+// on their 32-bit key (bits 32..63 of the composite), 8 bits per pass.  The
+// compaction left equal keys in index order, so stability gives the index
+// tie-break.  Per pass: block histograms (bin-major), one exclusive scan, and
+// a stable scatter that ranks equal digits by position inside each block.
+// ---------------------------------------------------------------------------
+constexpr int kRsItems = 2048;               // items per block (8 rounds of 256)
+
+__global__ void __launch_bounds__(kThreads) k_rs_hist(const unsigned long long* __restrict__ in,
+                                                      int64_t k, int shift, int nb,
+                                                      unsigned int* __restrict__ hist) {
+  __shared__ unsigned int h[256];
+  h[threadIdx.x] = 0u;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kRsItems;
+  for (int i = threadIdx.x; i < kRsItems; i += kThreads) {
+    const int64_t g = base + i;
+    if (g < k) atomicAdd(&h[(unsigned)(in[g] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];   // bin-major
+}
+
+__global__ void k_rs_scan(unsigned int* hist, int64_t total) {
+  __shared__ unsigned int sc[1024];
+  __shared__ unsigned int carry;
+  if (threadIdx.x == 0) carry = 0u;
+  __syncthreads();
+  for (int64_t base = 0; base < total; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const unsigned int v = i < total ? hist[i] : 0u;
+    sc[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const unsigned int t = threadIdx.x >= off ? sc[threadIdx.x - off] : 0u;
+      __syncthreads();
+      sc[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < total) hist[i] = carry + sc[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sc[1023];
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rs_scatter(const unsigned long long* __restrict__ in,
+                                                         unsigned long long* __restrict__ out,
+                                                         int64_t k, int shift, int nb,
+                                                         const unsigned int* __restrict__ offs) {
+  __shared__ unsigned int run[256];          // items of each digit already placed by this block
+  __shared__ unsigned int wc[kThreads / 32][256];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  run[threadIdx.x] = offs[(int64_t)threadIdx.x * nb + blockIdx.x];
+  const int64_t base = (int64_t)blockIdx.x * kRsItems;
+  for (int r = 0; r < kRsItems; r += kThreads) {
+    for (int i = threadIdx.x; i < (kThreads / 32) * 256; i += kThreads) (&wc[0][0])[i] = 0u;
+    __syncthreads();
+    const int64_t g = base + r + threadIdx.x;
+    const bool valid = g < k;
+    const unsigned long long v = valid ? in[g] : 0ull;
+    const unsigned int d = valid ? (unsigned)(v >> shift) & 255u : 256u + lane;   // no peers when invalid
+    const unsigned int peers = __match_any_sync(0xffffffffu, d);
+    const unsigned int lower = __popc(peers & ((1u << lane) - 1u));
+    if (valid && lower == 0) wc[warp][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      unsigned int before = run[d] + lower;
+      for (int w = 0; w < warp; ++w) before += wc[w][d];
+      out[before] = v;
+    }
+    __syncthreads();
+    {   // advance the running offsets by this round's counts
+      unsigned int add = 0u;
+      for (int w = 0; w < kThreads / 32; ++w) add += wc[w][threadIdx.x];
+      run[threadIdx.x] += add;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_unpack(const unsigned long long* __restrict__ items, int64_t k, int64_t* idx_out,
+                         float* snr_out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long v = items[i];
+    if (idx_out) idx_out[i] = (int64_t)(v & 0xffffffffull);
+    if (snr_out) snr_out[i] = key_nu((unsigned int)(v >> 32));
+  }
+}
+
 }  // namespace
 
 size_t topk_scratch_bytes(int64_t n, int64_t k) {
@@ -236,6 +331,10 @@ size_t topk_scratch_bytes(int64_t n, int64_t k) {
   b += (size_t)(2 * nblocks) * 4;
   b = (b + 15) & ~(size_t)15;
   b += (size_t)(k > 0 ? k : 1) * 8;
+  if (k > kSortMax) {   // radix sort: a second item buffer and the block histograms
+    const int64_t nb = (k + kRsItems - 1) / kRsItems;
+    b += (size_t)k * 8 + (size_t)256 * nb * 4 + 16;
+  }
   return b;
 }
 
@@ -245,7 +344,7 @@ cudaError_t launch_topk(const float* snr, int64_t n, int64_t k, void* scratch, s
                         int64_t* idx_out, float* snr_out, int* launches, cudaStream_t st) {
   if (k <= 0 || n <= 0) return cudaSuccess;
   if (k > n) k = n;
-  if (k > kSortMax || n > 0xffffffffll) return cudaErrorInvalidValue;
+  if (n > 0xffffffffll) return cudaErrorInvalidValue;
   if (scratch_bytes < topk_scratch_bytes(n, k)) return cudaErrorInvalidValue;
   const int64_t nblocks = (n + kChunk - 1) / kChunk;
   char* p = static_cast<char*>(scratch);
@@ -266,6 +365,24 @@ cudaError_t launch_topk(const float* snr, int64_t n, int64_t k, void* scratch, s
   k_compact_count<<<(unsigned)nblocks, kThreads, 0, st>>>(snr, n, sel, counts); ++L;
   k_compact_scan<<<1, 1024, 0, st>>>(counts, (int)nblocks); ++L;
   k_compact_scatter<<<(unsigned)nblocks, kThreads, 0, st>>>(snr, n, sel, counts, items); ++L;
+  if (k > kSortMax) {
+    const int nb = (int)((k + kRsItems - 1) / kRsItems);
+    unsigned long long* tmp = items + k;
+    unsigned int* hist = reinterpret_cast<unsigned int*>(tmp + k);
+    unsigned long long* a = items;
+    unsigned long long* b = tmp;
+    for (int pass = 0; pass < 4; ++pass) {
+      const int shift = 32 + 8 * pass;
+      k_rs_hist<<<nb, kThreads, 0, st>>>(a, k, shift, nb, hist); ++L;
+      k_rs_scan<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nb); ++L;
+      k_rs_scatter<<<nb, kThreads, 0, st>>>(a, b, k, shift, nb, hist); ++L;
+      unsigned long long* t = a; a = b; b = t;
+    }
+    // four passes: the sorted items are back in `items`
+    k_unpack<<<(unsigned)std::min<int64_t>((k + 255) / 256, 4096), 256, 0, st>>>(a, k, idx_out, snr_out); ++L;
+    if (launches) *launches += L;
+    return cudaGetLastError();
+  }
   int npow = 1;
   while (npow < k) npow <<= 1;
   const size_t smem = (size_t)npow * 8;

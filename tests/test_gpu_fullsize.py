@@ -130,6 +130,11 @@ def test_precision_variant_report(gpu, capsys):
     with capsys.disabled():
         for k, (mx, md, rc) in report.items():
             print(f"\nprecision {k}: max SNR err {mx:.2e}, median {md:.2e}, recall {rc:.2f}")
+    # each stored plane value carries <= u relative rounding error (u = 2^-8
+    # BF16, 2^-11 FP16), so |d nu| <= u (sum|psi_j| / sqrt(Phi) + |nu| / 2)
+    # <= u (sqrt(n) + 1.5) max(1, |nu|) with n the exposures of the orbit
+    n = sky.ex.n
     assert report["f32"][0] <= 1e-5
-    assert report["bf16"][0] <= 2.0 ** -7 and report["f16"][0] <= 2.0 ** -10
+    assert report["bf16"][0] <= 2.0 ** -8 * (np.sqrt(n) + 1.5)
+    assert report["f16"][0] <= 2.0 ** -11 * (np.sqrt(n) + 1.5)
     assert report["bf16"][2] == report["f32"][2] and report["f16"][2] == report["f32"][2]

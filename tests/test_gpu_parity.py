@@ -208,6 +208,10 @@ def test_plain_workload_stack_and_top100(gpu):
     # a k larger than the number of finite nu: the tail is the lowest-index -inf orbits
     idx2, val2 = gpu.topk(8192)
     check_topk(idx2, val2, nu, ref["n_amb"] > 0, 8192)
+    # large k (multi-block radix sort), up to every orbit of the batch
+    for k in (20000, len(sky.states)):
+        idx3, val3 = gpu.topk(k)
+        check_topk(idx3, val3, nu, ref["n_amb"] > 0, k)
 
 
 def _families(rng, n_orb, n_exp, n_fam):
