@@ -44,7 +44,7 @@ FP64_FLOP_PER_SAMPLE = 168.0
 FP64_PIPE_INST_PER_SAMPLE = 126.5
 # DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
 # measured on the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = 1.86e9 + 72e6   # full-size launch, ncu 1-pass dram__bytes
+TRAFFIC_BYTES_PER_LAUNCH = None   # re-measured with ncu after each change of the stack kernel
 
 
 def parse():
@@ -53,7 +53,10 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--fam-size", type=int, default=16384, help="orbits per injected asteroid")
+    p.add_argument("--workload", choices=["mba", "batched"], default="mba",
+                   help="mba: the MBA-scale survey (default); batched: uneven orbit families")
+    p.add_argument("--n-fam", type=int, default=4096, help="families of the batched workload")
+    p.add_argument("--fam-size", type=int, default=16384, help="orbits per family")
     p.add_argument("--n-true", type=int, default=1000)
     p.add_argument("--size", type=int, default=4096)
     p.add_argument("--n-exp", type=int, default=200)
@@ -131,10 +134,19 @@ class ClockSampler:
 def make_workload(args, rank, device):
     import torch
     from paper_2503_08854_gb300 import ndt, synth
+    stream = torch.cuda.Stream(device=device)
+    if args.workload == "batched":
+        sky = synth.batched_sky(n_fam=args.n_fam, fam_size=args.fam_size, seed=4 + rank)
+        imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
+        sky.fam_dev = tuple(torch.from_numpy(np.ascontiguousarray(x)).to(device)
+                            for x in sky.families)
+        states = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(device)
+        torch.cuda.synchronize(device)
+        return sky, stream, imgs, states
     sky = synth.mba_sky(n_exp=args.n_exp, size=args.size, n_true=args.n_true,
                         fam_size=args.fam_size, seed=2 + rank,
                         scale_arcsec=10.5 * 4096 / args.size)
-    stream = torch.cuda.Stream(device=device)
+    sky.fam_dev = None
     imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
     # injected sources at positions from the library's own position kernel
     ctx = ndt.create(device.index, stream)
@@ -173,7 +185,7 @@ def run_steps(ctx, stream, sky, imgs, states, k, n_steps, idx_out, snr_out, plan
         e2 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=plane)
-        ndt.stack_orbits(ctx, states, sky.t0, n)
+        ndt.stack_orbits(ctx, states, sky.t0, n, families=sky.fam_dev)
         ndt.topk_candidates(ctx, k, idx_out, snr_out)
         e2.record(stream)
         if vet is not None:
@@ -258,7 +270,7 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
             else:
                 ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=form.plane)
                 times = np.zeros(9, np.float32)
-                ndt.autotune(ctx, states, sky.t0, n, times_ms=times)
+                ndt.autotune(ctx, states, sky.t0, n, families=sky.fam_dev, times_ms=times)
                 st = ndt.get_stats(ctx)
                 ot, et = st["orbit_tile"], st["exp_tile"]
                 tiles = {"orbit_tile": ot, "exp_tile": et,
@@ -279,10 +291,12 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
         stats = ndt.get_stats(ctx)
         launches = stats["kernel_launches"] - launches0
         rec = recall_of(idx.cpu().numpy(), sky)
-        snr_all = torch.empty(n, device=device)     # untimed: one more stack for recall
-        ndt.stack_orbits(ctx, states, sky.t0, n, snr=snr_all)
-        ndt.synchronize(ctx)
-        rec_thr = recall_at_threshold(snr_all, sky)
+        rec_thr = None
+        if np.any(sky.inj_flux > 0):
+            snr_all = torch.empty(n, device=device)     # untimed: one more stack for recall
+            ndt.stack_orbits(ctx, states, sky.t0, n, families=sky.fam_dev, snr=snr_all)
+            ndt.synchronize(ctx)
+            rec_thr = recall_at_threshold(snr_all, sky)
         out = dict(step_ms=step_ms, stack_ms=stack_ms, vet_ms=vet_ms if vet else None,
                    wall_s=wall, launches=launches,
                    valid=stats["valid_samples"], samples=stats["samples"], recall=rec_thr,
@@ -315,7 +329,7 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
 
     def step():
         ndt.load_exposures(ctx, sky.ex, np_imgs, plane_dtype=form.plane)
-        ndt.stack_orbits(ctx, np_states, sky.t0, n)
+        ndt.stack_orbits(ctx, np_states, sky.t0, n, families=sky.families)
         ndt.topk_candidates(ctx, k, h_idx.numpy(), h_val.numpy())
 
     for _ in range(max(1, args.warmup)):
@@ -395,6 +409,17 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def workload_name(args, sky, states):
+    n = states.shape[1]
+    if args.workload == "batched":
+        fo, fe, _ = sky.families
+        return (f"batched uneven families: {len(fo) - 1} families x {args.fam_size} orbits "
+                f"(NEO/MBA/KBO), {int((fe[1:] - fe[:-1]).min())}-{int((fe[1:] - fe[:-1]).max())} "
+                f"of {sky.ex.n} exposures {int(sky.ex.width[0])}^2 each, top-{min(args.k, n)}")
+    return (f"MBA-scale survey: {sky.ex.n} exposures {args.size}x{args.size}, {n} candidate "
+            f"orbits ({args.n_true} families), all orbits x all exposures, top-{min(args.k, n)}")
+
+
 # ------------------------------------------------------------------- main ----
 
 def main():
@@ -428,6 +453,8 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     vet_params, vet_info = None, None
+    if args.workload == "batched":
+        args.no_vet = True      # no injected sources to vet in the batched workload
     if "chosen" in args.forms.split(",") and not args.no_vet:
         vet_params, vet_info = train_vetter(device, n_train_sky=args.vet_skies,
                                             n_test_sky=max(1, args.vet_skies // 4))
@@ -453,9 +480,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"MBA-scale survey: {sky.ex.n} exposures {args.size}x{args.size}, "
-                               f"{states.shape[1]} candidate orbits ({args.n_true} families), "
-                               f"all orbits x all exposures, top-{min(args.k, states.shape[1])}",
+        "config": {"workload": workload_name(args, sky, states),
                    "form": head, "planes": forms[head].plane,
                    "launch": forms[head].mode + ("+graph" if forms[head].graph else ""),
                    "tiles": r["tiles"], "l2": "inputs larger than L2 (planes >= 13 GB)",

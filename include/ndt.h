@@ -55,8 +55,10 @@ typedef enum {
 
 typedef enum {
   NDT_PLANE_F32 = 0,  /* psi, phi stored as FP32                             */
-  NDT_PLANE_BF16 = 1, /* BF16 values times a per-exposure FP32 scale         */
-  NDT_PLANE_F16 = 2   /* FP16 values times a per-exposure FP32 scale         */
+  NDT_PLANE_BF16 = 1, /* BF16 values times per-exposure FP32 scales: the
+                         noise sigma of psi and the interior value of phi  */
+  NDT_PLANE_F16 = 2   /* FP16 values times per-exposure FP32 scales that map
+                         each plane's largest magnitude to 2^14            */
 } ndt_plane_dtype;
 
 typedef enum {
@@ -228,7 +230,9 @@ ndt_status ndt_stamps(ndt_ctx *ctx, const double *states, double t0, int64_t n_o
    linear 32->1 giving a logit. */
 int64_t ndt_cnn_param_count(void);
 
-/* Logits of n BF16 stamps [n][2][21][21] (FP32 accumulation). */
+/* Logits of n BF16 stamps [n][2][21][21] on the tensor core: layers 2 and 3
+   take BF16 weights and BF16 activations with FP32 accumulation (layer 1 is
+   FP32).  NDT_ETIMEOUT if a bounded device wait gave up (logits then NaN). */
 ndt_status ndt_cnn_forward(ndt_ctx *ctx, const float *params, const uint16_t *stamps_bf16,
                            int64_t n, float *logits);
 

@@ -140,13 +140,24 @@ def conv2d(x, w, b):
     return y.reshape(B, O, H, W) + b[None, :, None, None]
 
 
-def forward(theta, x, keep=False):
-    """Logits (B,) of the network; with keep=True also the activations."""
+def bf16_round(a):
+    """Round to BF16 (round-to-nearest-even, through FP32 first), as FP64."""
+    u = np.asarray(a, np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(theta, x, keep=False, bf16_hidden=False):
+    """Logits (B,) of the network; with keep=True also the activations.
+    bf16_hidden=True gives the scoring variant: the weights of layers 2 and 3
+    and the activations entering them are rounded to BF16 (accumulation stays
+    exact here)."""
     p = unpack(theta)
     x = np.asarray(x, np.float64)
-    y1 = conv2d(x, p["w1"], p["b1"]); a1 = np.maximum(y1, 0)
-    y2 = conv2d(a1, p["w2"], p["b2"]); a2 = np.maximum(y2, 0)
-    y3 = conv2d(a2, p["w3"], p["b3"]); a3 = np.maximum(y3, 0)
+    rnd = bf16_round if bf16_hidden else (lambda a: a)
+    y1 = conv2d(x, p["w1"], p["b1"]); a1 = rnd(np.maximum(y1, 0))
+    y2 = conv2d(a1, rnd(p["w2"]), p["b2"]); a2 = rnd(np.maximum(y2, 0))
+    y3 = conv2d(a2, rnd(p["w3"]), p["b3"]); a3 = np.maximum(y3, 0)
     g = a3.mean(axis=(2, 3))
     z = g @ p["wl"] + p["bl"][0]
     if keep:

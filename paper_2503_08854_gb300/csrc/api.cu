@@ -309,11 +309,18 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
       double w[2 * kMaxPsfRadius + 1], sum = 0.0;
       const double s2 = 2.0 * (double)m.psf_sigma_px * (double)m.psf_sigma_px;
       for (int k = -J.R; k <= J.R; ++k) sum += (w[k + J.R] = std::exp(-(double)(k * k) / s2));
+      double sg2 = 0.0;
       for (int k = 0; k <= 2 * J.R; ++k) {
         const double g = w[k] / sum;
         J.g[k] = (float)g;
         J.g2[k] = (float)(g * g);
+        sg2 += g * g;
       }
+      // BF16 scales: the noise sigma of psi, sqrt(sum P^2 / V), and the
+      // interior value of phi, sum P^2 / V (sum P^2 = (sum g^2)^2)
+      const double vbar = variances ? 1.0 : (double)J.var_c;
+      J.s_phi = (float)(sg2 * sg2 / vbar);
+      J.s_psi = (float)std::sqrt(sg2 * sg2 / vbar);
     }
     J.W = m.width;
     J.H = m.height;
@@ -368,22 +375,30 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneStoreF32,
                          ctx->planes.p, nullptr, ctx->stream), "plane kernel");
     ctx->launches += 1;
+  } else if (plane_dtype == NDT_PLANE_BF16) {
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var,
+                         kPlaneStoreBF16, ctx->planes.p, nullptr, ctx->stream), "plane kernel");
+    ctx->launches += 1;
+    for (int s = 0; s < n_exp; ++s) {
+      ctx->ex_host[s].s_psi = jobs[s].s_psi;
+      ctx->ex_host[s].s_phi = jobs[s].s_phi;
+    }
   } else {
     // pass 1: largest |psi| and phi per plane (nothing stored); pass 2: the
-    // same planes again, written as 16-bit pairs scaled by those maxima
+    // same planes again, written as FP16 pairs scaled by those maxima
     NDT_CK(ctx->absmax_dev.ensure(8 * n_exp), "absmax");
     NDT_CK(cudaMemsetAsync(ctx->absmax_dev.p, 0, 8 * n_exp, ctx->stream), "memset");
     NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneAbsMax, nullptr,
                          ctx->absmax_dev.as<unsigned int>(), ctx->stream), "plane max kernel");
     NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var,
-                         plane_dtype == NDT_PLANE_BF16 ? kPlaneStoreBF16 : kPlaneStoreF16,
+                         kPlaneStoreF16,
                          ctx->planes.p, ctx->absmax_dev.as<unsigned int>(), ctx->stream),
            "plane kernel");
     ctx->launches += 2;
   }
   record(ctx, 1);
   ctx->have_planes_ev = true;
-  if (plane_dtype != NDT_PLANE_F32) {
+  if (plane_dtype == NDT_PLANE_F16) {
     std::vector<unsigned int> mx(2 * n_exp);
     NDT_CK(cudaMemcpyAsync(mx.data(), ctx->absmax_dev.p, 8 * n_exp, cudaMemcpyDeviceToHost,
                            ctx->stream), "scale read-back");
@@ -665,7 +680,7 @@ ndt_status ndt_predict_positions(ndt_ctx* ctx, const double* states, double t0, 
     NDT_CK(ctx->xy_tmp.ensure(bytes), "position scratch");
     dst = ctx->xy_tmp.as<double>();
   }
-  NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+  NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
   NDT_CK(launch_predict(static_cast<const double*>(st_dev), n_orbits, t0, ctx->ex_dev.as<ExpDev>(),
                         ctx->pos_to_table_dev.as<int32_t>(), ctx->n_exp, ctx->ph, dst,
                         ctx->counters.as<unsigned long long>(), ctx->stream), "predict kernel");
@@ -775,6 +790,19 @@ ndt_status copy_out(ndt_ctx* ctx, T* user, const T* dev, size_t count) {
   return NDT_OK;
 }
 
+// Timeout flag of the tensor-core forward (an int after the two counters).
+int* cnn_err(ndt_ctx* ctx) { return reinterpret_cast<int*>(ctx->counters.as<unsigned long long>() + 2); }
+
+ndt_status check_cnn_err(ndt_ctx* ctx) {
+  int e = 0;
+  NDT_CK(cudaMemcpy(&e, cnn_err(ctx), sizeof e, cudaMemcpyDeviceToHost), "flag read");
+  if (e) {
+    NDT_CK(cudaMemset(cnn_err(ctx), 0, sizeof e), "flag reset");
+    return fail(ctx, NDT_ETIMEOUT, "tensor-core CNN forward: a bounded wait timed out");
+  }
+  return NDT_OK;
+}
+
 ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
                        const int64_t* cand_idx, int64_t n_cand, float* f32_dev,
                        __nv_bfloat16* bf16_dev) {
@@ -789,7 +817,8 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
   s = to_device(ctx, cand_idx, sizeof(int64_t) * n_cand, ctx->cand_stage, &cd);
   if (s != NDT_OK) return s;
   NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp), "stamp positions");
-  NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+  // reset the failure counter only: the valid-sample count of the last stack stays
+  NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
   NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0,
                                 static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
                                 ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(),
@@ -840,12 +869,12 @@ ndt_status ndt_cnn_forward(ndt_ctx* ctx, const float* params, const uint16_t* st
   float* lo = nullptr;
   if (s == NDT_OK) s = out_buffer(ctx, logits, n, ctx->cnn_out, &lo);
   if (s != NDT_OK) return s;
-  NDT_CK(launch_cnn_forward(static_cast<const float*>(th), static_cast<const __nv_bfloat16*>(x), n, lo,
-                            ctx->n_sms, ctx->stream), "CNN forward");
+  NDT_CK(launch_cnn_forward_tc(static_cast<const float*>(th), static_cast<const __nv_bfloat16*>(x), n, lo,
+                               cnn_err(ctx), ctx->n_sms, ctx->stream), "CNN forward");
   ctx->launches += 1;
   if ((s = copy_out(ctx, logits, lo, n)) != NDT_OK) return s;
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
-  return NDT_OK;
+  return check_cnn_err(ctx);
 }
 
 ndt_status ndt_cnn_loss_grad(ndt_ctx* ctx, const float* params, const uint16_t* stamps_bf16,
@@ -920,13 +949,13 @@ ndt_status ndt_vet(ndt_ctx* ctx, const float* params, const double* states, doub
   float* lo = nullptr;
   if (s == NDT_OK) s = out_buffer(ctx, scores, n_cand, ctx->cnn_out, &lo);
   if (s != NDT_OK) return s;
-  NDT_CK(launch_cnn_forward(static_cast<const float*>(th), ctx->stamp_bf16.as<__nv_bfloat16>(), n_cand,
-                            lo, ctx->n_sms, ctx->stream), "CNN forward");
+  NDT_CK(launch_cnn_forward_tc(static_cast<const float*>(th), ctx->stamp_bf16.as<__nv_bfloat16>(), n_cand,
+                               lo, cnn_err(ctx), ctx->n_sms, ctx->stream), "CNN forward");
   NDT_CK(launch_sigmoid(lo, n_cand, ctx->stream), "sigmoid");
   ctx->launches += 2;
   if ((s = copy_out(ctx, scores, lo, n_cand)) != NDT_OK) return s;
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
-  return NDT_OK;
+  return check_cnn_err(ctx);
 }
 
 ndt_status ndt_get_stats(ndt_ctx* ctx, ndt_stats* out) {

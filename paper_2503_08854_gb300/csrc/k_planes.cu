@@ -7,11 +7,12 @@
 // separable correlations (zero padding factorises too).  One CTA computes one
 // 32 x 32 output tile from a (32+2R)^2 input tile in shared memory and writes
 // it as one contiguous tile of the tile-major (psi, phi) plane.  The window
-// weights come precomputed with the job.  FP32 planes take one pass (4 bytes
-// read, 8 with a variance plane, and 8 written per pixel); BF16/FP16 planes
-// take two: a pass that only reduces the largest |psi| and phi of each plane,
-// then the same computation writing 16-bit pairs scaled by those maxima
-// (8 bytes read and 4 written per pixel).
+// weights come precomputed with the job.  FP32 planes: one pass, 4 bytes read
+// (8 with a variance plane) and 8 written per pixel.  BF16 planes: one pass
+// writing 4 bytes per pixel, values divided by a-priori per-exposure scales
+// (BF16 has the FP32 exponent range, so no data-dependent range is needed).
+// FP16 planes: two passes, one reducing the largest |psi| and phi of each
+// plane, one writing 16-bit pairs scaled so those maxima map to 2^14.
 #include "ndt_internal.cuh"
 
 namespace ndt {
@@ -93,7 +94,10 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
   }
   __syncthreads();
   float s0 = 1.0f, s1 = 1.0f, m0 = 0.0f, m1 = 0.0f;
-  if (MODE == kPlaneStoreBF16 || MODE == kPlaneStoreF16) {
+  if (MODE == kPlaneStoreBF16) {
+    s0 = J.s_psi;
+    s1 = J.s_phi;
+  } else if (MODE == kPlaneStoreF16) {
     const float a0 = __uint_as_float(absmax2[2 * blockIdx.y]);
     const float a1 = __uint_as_float(absmax2[2 * blockIdx.y + 1]);
     s0 = a0 > 0.0f ? a0 / 16384.0f : 1.0f;
@@ -128,11 +132,22 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     }
   }
   if (MODE == kPlaneAbsMax) {
+    // reduce over the CTA first: one atomic per CTA and plane
+    __shared__ float red[2][kThreads / 32];
     for (int o = 16; o > 0; o >>= 1) {
       m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, o));
       m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, o));
     }
     if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = m0;
+      red[1][threadIdx.x >> 5] = m1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < kThreads / 32; ++w) {
+        m0 = fmaxf(m0, red[0][w]);
+        m1 = fmaxf(m1, red[1][w]);
+      }
       atomicMax(absmax2 + 2 * blockIdx.y, __float_as_uint(m0));
       atomicMax(absmax2 + 2 * blockIdx.y + 1, __float_as_uint(m1));
     }

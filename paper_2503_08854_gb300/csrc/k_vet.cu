@@ -14,6 +14,8 @@
 //
 // Network.  x (2,21,21) BF16 -> conv5x5 2->32 -> ReLU -> conv5x5 32->32 ->
 // ReLU -> conv5x5 32->32 -> ReLU -> global average pool -> linear 32->1.
+// This file holds the training pass (loss and gradients, FP32 throughout);
+// scoring runs on the tensor core (k_cnn_tc.cu).
 // One CTA owns one stamp at a time; activations live in shared memory as
 // zero-padded 25 x 25 planes, weights of 8 output channels at a time are
 // staged in shared memory, and each thread accumulates 8 channels x 2 pixels
@@ -325,20 +327,6 @@ __device__ void weight_grad(float* sm, const float* in, const float* dy, const f
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kVetThreads) k_cnn_forward(const float* __restrict__ th,
-                                                             const __nv_bfloat16* __restrict__ x,
-                                                             int64_t n, float* __restrict__ logits) {
-  extern __shared__ float sm[];
-  clear_smem(sm);
-  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
-    __syncthreads();
-    load_stamp(sm, x, b);
-    __syncthreads();
-    const float z = cnn_forward_cta(sm, th);
-    if (threadIdx.x == 0) logits[b] = z;
-  }
-}
-
 // Loss and gradient of the mean BCE over the batch: grad must be zeroed and
 // loss_sum set to 0 before the launch; a1_scratch holds CH x 441 floats per CTA.
 __global__ void __launch_bounds__(kVetThreads) k_cnn_backward(const float* __restrict__ th,
@@ -452,17 +440,6 @@ cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int
     k_stamps<kBF16><<<blocks, kVetThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   else
     k_stamps<kF16><<<blocks, kVetThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cnn_forward(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
-                               int n_sms, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_cnn_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kCnnSmem);
-  if (e != cudaSuccess) return e;
-  const unsigned blocks = (unsigned)std::min<int64_t>(n, n_sms);
-  k_cnn_forward<<<blocks, kVetThreads, kCnnSmem, st>>>(th, x, n, logits);
   return cudaGetLastError();
 }
 

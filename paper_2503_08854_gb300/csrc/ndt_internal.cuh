@@ -151,6 +151,7 @@ struct OrbitConst {
   double period;       // orbital period (bound orbits), else 0
   double inv_period;
   double half_period;  // steps longer than this are reduced modulo the period
+  double series_dt;    // steps shorter than this use the truncated f/g series
 };
 
 __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
@@ -168,7 +169,71 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     oc.inv_period = 0.0;
     oc.half_period = 1e300;
   }
+  // Bound for the f/g series: along the whole conic |u| = GM/r^3 <= GM/q^3,
+  // |p| = |r.v|/r^2 <= v_q/q and |w| = |v^2/r^2 - u| <= v_q^2/q^2 + GM/q^3,
+  // with q the perihelion distance and v_q the speed there (vis-viva).  With
+  // K = GM/q^3 + v_q^2/q^2 and dt^2 K <= 1e-7 the neglected terms of the
+  // series stay at FP64 rounding (see fg_series_step).
+  {
+    const double hx = r[1] * v[2] - r[2] * v[1], hy = r[2] * v[0] - r[0] * v[2],
+                 hz = r[0] * v[1] - r[1] * v[0];
+    const double semi_latus = (hx * hx + hy * hy + hz * hz) * ph.inv_gm;
+    const double ecc = sqrt(fmax(0.0, 1.0 - semi_latus * oc.alpha));
+    const double q = semi_latus / (1.0 + ecc);
+    const double vq2 = ph.gm * (2.0 / q - oc.alpha);
+    const double K = ph.gm / (q * q * q) + vq2 / (q * q);
+    oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
+  }
   return oc;
+}
+
+// ---------------------------------------------------------------------------
+// Short steps: the Lagrange f and g series about the current state (e.g.
+// Bate, Mueller & White 1971, sec. 4.5; Danby 1988, sec. 6.9), with
+// u = GM/r^3, p = (r.v)/r^2, w = v^2/r^2 - u:
+//   f = 1 - u t^2/2 + u p t^3/2 + u (3w - 15p^2 + u) t^4/24
+//   g = t - u t^3/6 + u p t^4/4
+//   fdot = -u t + 3 u p t^2/2 + u (3w - 15p^2 + u) t^3/6
+//   gdot = 1 - u t^2/2 + u p t^3
+// Used only when dt^2 K <= 1e-7 (K bounds u, p^2 and |w| along the conic):
+// the neglected terms are then O((dt^2 K)^(5/2)) relative, and a sweep of
+// random conics at the bound against the universal-variable solver shows
+// relative errors of 6e-16, so the step is exact to FP64 rounding without a
+// Kepler solve (about an hour for main-belt orbits, seconds near a close
+// perihelion).  1/|r| of the new state starts from the first-order
+// prediction (1/r)(1 - p t), whose relative error is O(dt^2 K) <= 1e-7, and
+// takes two Newton steps y <- y (3 - x y^2)/2 (error ~ (3/2) e^2 per step,
+// so below 1e-20 after two).
+// ---------------------------------------------------------------------------
+// Products with these replace divisions by 6 and 24 (an FP64 division is a
+// multi-instruction sequence on the FP64 pipe); they only scale correction
+// terms, so their last-bit rounding does not matter.
+constexpr double kInv6 = 1.0 / 6.0;
+constexpr double kInv24 = 1.0 / 24.0;
+
+__device__ __forceinline__ void fg_series_step(const Phys& ph, double t, double r[3], double v[3],
+                                               double& rn, double& inv_r) {
+  const double ir2 = inv_r * inv_r;
+  const double u = ph.gm * ir2 * inv_r;
+  const double p = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ir2;
+  const double w = fma(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], ir2, -u);
+  const double t2 = t * t, t3 = t2 * t;
+  const double c4 = u * fma(3.0, w, fma(-15.0 * p, p, u));     // u (3w - 15p^2 + u)
+  const double up = u * p;
+  const double f = 1.0 + fma(-0.5 * u, t2, fma(0.5 * up, t3, (c4 * kInv24) * (t2 * t2)));
+  const double g = t + fma(-u * kInv6, t3, 0.25 * up * (t2 * t2));
+  const double fdot = fma(-u, t, fma(1.5 * up, t2, (c4 * kInv6) * t3));
+  const double gdot = 1.0 + fma(-0.5 * u, t2, up * t3);
+  double rr[3];
+  for (int i = 0; i < 3; ++i) rr[i] = fma(f, r[i], g * v[i]);
+  for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], gdot * v[i]);
+  for (int i = 0; i < 3; ++i) r[i] = rr[i];
+  const double x = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  double y = inv_r * fma(-p, t, 1.0);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) y = y * fma(-0.5 * x * y, y, 1.5);
+  inv_r = y;
+  rn = x * y;
 }
 
 // ---------------------------------------------------------------------------
@@ -200,6 +265,10 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     inv_r = 1.0 / rn;
     return 0;
   }
+  if (fabs(dt) <= oc.series_dt) {
+    fg_series_step(ph, dt, r, v, rn, inv_r);
+    return 0;
+  }
   if (fabs(dt) > oc.half_period) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
   const double alpha = oc.alpha;
   const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ph.inv_sqrt_gm;
@@ -208,7 +277,7 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   // third-order series of chi(dt): u - sig0 u^2/(2 r0) - u^3/6 (1/r0 - alpha - 3 sig0^2/r0^2)
   const double u = sdt * inv_r;
   const double si = sig0 * inv_r;
-  double chi = u * fma(u, fma(-(u / 6.0), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
+  double chi = u * fma(u, fma(-(u * kInv6), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
   if (fabs(alpha) * chi * chi > 0.25 || !(fabs(chi) < 1e30)) {
     chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
   }
@@ -329,7 +398,7 @@ struct PlaneJob {
   int32_t W, H, tiles_x, tiles_y;
   int64_t plane_off;    // element offset in the plane buffer
   int32_t R;            // window radius ceil(4 sigma)
-  int32_t pad_;
+  float s_psi, s_phi;   // a-priori scales of the BF16 planes (noise sigma of psi, interior phi)
   float g[2 * kMaxPsfRadius + 1];    // unit-sum 1-D Gaussian window (host FP64, rounded)
   float g2[2 * kMaxPsfRadius + 1];   // its square
 };
@@ -388,8 +457,8 @@ cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, c
 cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                           const void* planes, int plane_type, float* out_f32,
                           __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st);
-cudaError_t launch_cnn_forward(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
-                               int n_sms, cudaStream_t st);
+cudaError_t launch_cnn_forward_tc(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
+                                  int* err, int n_sms, cudaStream_t st);
 cudaError_t launch_cnn_backward(const float* th, const __nv_bfloat16* x, const float* labels,
                                 int64_t n, float* grad, float* loss_sum, float* a1_scratch,
                                 float* logits, int n_sms, cudaStream_t st);

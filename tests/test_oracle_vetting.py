@@ -127,3 +127,14 @@ def test_toy_problem_is_learned():
     z = V.forward(theta, x)
     assert V.bce_with_logits(z, y) < 0.5 * loss0
     assert np.all((z > 0) == (y == 1))
+
+
+def test_bf16_rounding_matches_library():
+    """The oracle's BF16 rounding (for the scoring variant) equals torch's
+    round-to-nearest-even conversion, ties included."""
+    import torch
+    rng = np.random.default_rng(4)
+    a = np.concatenate([rng.normal(size=5000) * 10.0 ** rng.integers(-5, 5, 5000),
+                        [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -1.0 - 2.0 ** -8, 0.0, 1e-30]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(V.bf16_round(a), ref)
