@@ -34,17 +34,16 @@ UNIT = "samples/s"
 # FP64 peak of one GB300 derived from unit counts and clock: 152 SMs x 2 FP64
 # FMA per SM per clock x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# FP64 flops executed per (orbit, exposure) sample by the stack kernel on this
-# workload, from ncu instruction counters (DFMA x 2 + DADD + DMUL) divided by
-# the samples of the captured launch (MBA-scale workload at 512 orbits per
-# family, 1024 x 1024 images: 63.5 DFMA + 34.1 DMUL + 6.8 DADD per sample).
-# The FP64 pipe also issues conversions and compares (126.5 FP64-pipe thread
-# instructions per sample in all), roofline section.
-FP64_FLOP_PER_SAMPLE = 168.0
-FP64_PIPE_INST_PER_SAMPLE = 126.5
+# FP64 flops executed per computed (orbit, exposure) sample by the stack
+# kernel, from ncu instruction counters (DFMA x 2 + DADD + DMUL) over the
+# samples whose FP64 work ran in the captured launch (samples minus those the
+# off-chip test removed), and the FP64-pipe thread instructions per computed
+# sample (conversions and compares included).  MBA: workload at 512 orbits per
+# family and 1024 x 1024 images; batched: 128 families and 512 x 512 images.
+FP64_PER_SAMPLE = {"mba": (143.6, 110.6), "batched": (147.9, 114.7)}
 # DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
 # measured on the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = None   # re-measured with ncu after each change of the stack kernel
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
 
 
 def parse():
@@ -58,7 +57,8 @@ def parse():
     p.add_argument("--n-fam", type=int, default=4096, help="families of the batched workload")
     p.add_argument("--fam-size", type=int, default=16384, help="orbits per family")
     p.add_argument("--n-true", type=int, default=1000)
-    p.add_argument("--size", type=int, default=4096)
+    p.add_argument("--size", type=int, default=None,
+                   help="image side (default 4096 for mba, 2048 for batched)")
     p.add_argument("--n-exp", type=int, default=200)
     p.add_argument("--k", type=int, default=8192)
     p.add_argument("--plane", default="bf16", choices=["f32", "bf16", "f16"])
@@ -69,7 +69,10 @@ def parse():
     p.add_argument("--tiles", default=None, help="fixed OT,ET for the persistent form (no autotune)")
     p.add_argument("--no-vet", action="store_true", help="skip the CNN vetting stage")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.size is None:
+        a.size = 2048 if a.workload == "batched" else 4096
+    return a
 
 
 # ----------------------------------------------------------------- clocks ----
@@ -136,7 +139,8 @@ def make_workload(args, rank, device):
     from paper_2503_08854_gb300 import ndt, synth
     stream = torch.cuda.Stream(device=device)
     if args.workload == "batched":
-        sky = synth.batched_sky(n_fam=args.n_fam, fam_size=args.fam_size, seed=4 + rank)
+        sky = synth.batched_sky(n_fam=args.n_fam, fam_size=args.fam_size, seed=4 + rank,
+                                size=args.size, scale_arcsec=60.0 * 2048 / args.size)
         imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
         sky.fam_dev = tuple(torch.from_numpy(np.ascontiguousarray(x)).to(device)
                             for x in sky.families)
@@ -298,7 +302,7 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
             ndt.synchronize(ctx)
             rec_thr = recall_at_threshold(snr_all, sky)
         out = dict(step_ms=step_ms, stack_ms=stack_ms, vet_ms=vet_ms if vet else None,
-                   wall_s=wall, launches=launches,
+                   wall_s=wall, launches=launches, skipped=stats["offchip_skipped"],
                    valid=stats["valid_samples"], samples=stats["samples"], recall=rec_thr,
                    recall_topk=rec,
                    planes_ms=stats["last_planes_ms"], topk_ms=stats["last_topk_ms"], tiles=tiles,
@@ -503,17 +507,22 @@ def main():
                       "stack_ms": statistics.mean(res["stack_ms"]), "planes_ms": res["planes_ms"],
                       "topk_ms": res["topk_ms"], "recall": res["recall"],
                       "recall_in_topk": res["recall_topk"],
-                      "valid_fraction": res["valid"] / max(res["samples"], 1)}
+                      "valid_fraction": res["valid"] / max(res["samples"], 1),
+                      "offchip_skipped_fraction": res["skipped"] / max(res["samples"], 1)}
     stack_s = statistics.mean(r["stack_ms"]) / 1e3
-    if FP64_FLOP_PER_SAMPLE is not None:
-        ach = FP64_FLOP_PER_SAMPLE * samples / stack_s / 1e12
+    flop_per_sample, inst_per_sample = FP64_PER_SAMPLE[args.workload]
+    # FP64 work runs only for the samples the off-chip test did not remove
+    computed = samples - r["skipped"]
+    if flop_per_sample is not None:
+        ach = flop_per_sample * computed / stack_s / 1e12
         # FP64 pipe issue rate: 2 thread instructions / clock / SM
-        pipe_frac = FP64_PIPE_INST_PER_SAMPLE * samples / stack_s / (152 * 2 * 2.07e9)
+        pipe_frac = inst_per_sample * computed / stack_s / (152 * 2 * 2.07e9)
         line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
                             "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                            "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(args.workload),
                             "kernel": "stack kernel (FP64 pipe)",
                             "fp64_pipe_issue_frac": pipe_frac,
+                            "fp64_samples_per_launch": computed,
                             "algorithmic_bytes_per_launch":
                                 (8 if forms[head].plane == "f32" else 4) * r["valid"]}
     else:

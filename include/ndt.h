@@ -96,6 +96,8 @@ typedef struct {
   int32_t exp_tile;
   int32_t launch_mode;
   int32_t plane_dtype;
+  int64_t offchip_skipped;   /* samples of the last stack whose FP64 work the
+                                off-chip test removed (persistent form)     */
 } ndt_stats;
 
 typedef struct ndt_ctx ndt_ctx;
@@ -192,6 +194,18 @@ ndt_status ndt_get_planes(ndt_ctx *ctx, int32_t j, float *psi_out, float *phi_ou
    captured CUDA graph when the arguments repeat. */
 ndt_status ndt_set_launch(ndt_ctx *ctx, int32_t mode, int32_t orbit_tile, int32_t exp_tile,
                           int32_t use_graph);
+
+/* Off-chip test of the persistent form (on by default; the plain form never
+   uses it).  Before the FP64 step of a sample, an FP32 second-order
+   prediction of its pixel with a rigorous error bound (Taylor remainder from
+   the orbit's perihelion jerk bound, light time, FP32 rounding, TAN stretch)
+   is compared with the image; when every lane of a warp is certainly off
+   the chip the warp skips the sample and the next computed step starts from
+   the last computed state.  The stacked sums are those of the full
+   computation (skipped samples are out of bounds); only the rounding of the
+   chained state differs.  No counterpart in the paper: its Algorithm 1
+   propagates every (orbit, image) pair.  enabled = 0 switches it off. */
+ndt_status ndt_set_offchip_test(ndt_ctx *ctx, int32_t enabled);
 
 /*
  * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}

@@ -147,15 +147,16 @@ def bf16_round(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def forward(theta, x, keep=False, bf16_hidden=False):
+def forward(theta, x, keep=False, bf16_operands=False):
     """Logits (B,) of the network; with keep=True also the activations.
-    bf16_hidden=True gives the scoring variant: the weights of layers 2 and 3
-    and the activations entering them are rounded to BF16 (accumulation stays
-    exact here)."""
+    bf16_operands=True gives the scoring variant, whose convolution operands
+    are BF16: the weights of all three layers and the activations entering
+    layers 2 and 3 are rounded to BF16 (the stamps already are BF16); sums,
+    biases, pooling and the head stay exact here."""
     p = unpack(theta)
     x = np.asarray(x, np.float64)
-    rnd = bf16_round if bf16_hidden else (lambda a: a)
-    y1 = conv2d(x, p["w1"], p["b1"]); a1 = rnd(np.maximum(y1, 0))
+    rnd = bf16_round if bf16_operands else (lambda a: a)
+    y1 = conv2d(x, rnd(p["w1"]), p["b1"]); a1 = rnd(np.maximum(y1, 0))
     y2 = conv2d(a1, rnd(p["w2"]), p["b2"]); a2 = rnd(np.maximum(y2, 0))
     y3 = conv2d(a2, rnd(p["w3"]), p["b3"]); a3 = np.maximum(y3, 0)
     g = a3.mean(axis=(2, 3))

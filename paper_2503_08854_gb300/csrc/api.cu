@@ -74,6 +74,8 @@ struct ndt_ctx {
       cnn_params, cnn_grad;
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
+  int32_t offchip = 1;     // off-chip test of the persistent form
+  double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
   // stats
@@ -168,6 +170,29 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   to_ecl(ay, e.ay);
   e.crpix[0] = m.crpix[0];
   e.crpix[1] = m.crpix[1];
+  // FP32 copies for the off-chip test; ppr = largest singular value of
+  // CD^-1 (px/deg) in px/rad: the TAN map's stretch at the tangent point
+  for (int i = 0; i < 3; ++i) {
+    e.p0_f[i] = (float)e.p0[i];
+    e.ax_f[i] = (float)e.ax[i];
+    e.ay_f[i] = (float)e.ay[i];
+  }
+  e.crpix_f[0] = (float)m.crpix[0];
+  e.crpix_f[1] = (float)m.crpix[1];
+  const double fro = i00 * i00 + i01 * i01 + i10 * i10 + i11 * i11, dt = i00 * i11 - i01 * i10;
+  const double smax = std::sqrt(0.5 * (fro + std::sqrt(std::max(0.0, fro * fro - 4.0 * dt * dt))));
+  e.ppr = (float)(smax * r2d * (1.0 + 1e-6));
+  // largest off-axis angle of the chip: at a corner of [-1/2, W-1/2] x
+  // [-1/2, H-1/2] (the TAN radius grows with the angle)
+  double rmax = 0.0;
+  for (int c = 0; c < 4; ++c) {
+    const double px = (c & 1 ? m.width : 0) - 0.5 - m.crpix[0];
+    const double py = (c & 2 ? m.height : 0) - 0.5 - m.crpix[1];
+    const double xi = m.cd[0] * px + m.cd[1] * py, eta = m.cd[2] * px + m.cd[3] * py;   // deg
+    rmax = std::max(rmax, std::sqrt(xi * xi + eta * eta) / r2d);
+  }
+  const double th = std::atan(rmax) + 0.01;
+  e.cos_far = th < 0.5 * kPi ? (float)(std::cos(th) * (1.0 - 1e-6)) : -2.0f;
 }
 
 void record(ndt_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
@@ -279,6 +304,7 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
                    [&](int a, int b) { return meta[a].mjd < meta[b].mjd; });
   ctx->table_to_sorted.assign(n_exp, 0);
   for (int s = 0; s < n_exp; ++s) ctx->table_to_sorted[ctx->sorted_to_table[s]] = s;
+  ctx->t_ref = meta[ctx->sorted_to_table[0]].mjd;
 
   // plane layout (sorted order), staging of host images
   ctx->ex_host.assign(n_exp, ExpDev{});
@@ -291,6 +317,8 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     e.t = m.mjd;
     for (int i = 0; i < 3; ++i) e.obs[i] = m.obs_xyz[i];
     derive_projection(m, ctx->obliquity, e);
+    e.tf = (float)(m.mjd - ctx->t_ref);
+    for (int i = 0; i < 3; ++i) e.obs_f[i] = (float)m.obs_xyz[i];
     e.W = m.width;
     e.H = m.height;
     e.tiles_x = (m.width + kTile - 1) / kTile;
@@ -525,6 +553,7 @@ ndt_status prepare_families(ndt_ctx* ctx, int64_t n, const int64_t* fo_in, const
 ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
   if (ctx->mode == NDT_LAUNCH_PLAIN) {
     NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
+    NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 8, ctx->stream), "memset");
     record(ctx, 2);
     NDT_CK(launch_stack_plain(a, ctx->stream), "stack kernel");
     record(ctx, 3);
@@ -536,6 +565,7 @@ ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(ctx->queue_head.p, 0, 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 8, ctx->stream);
     if (e == cudaSuccess) e = launch_stack_persistent(a, ctx->n_sms, ctx->stream);
     return e;
   };
@@ -615,6 +645,8 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   a.min_obs = min_obs;
   a.counters = ctx->counters.as<unsigned long long>();
   a.ph = ctx->ph;
+  a.t_ref = ctx->t_ref;
+  a.offchip_test = persistent ? ctx->offchip : 0;
   s = run_stack(ctx, a);
   if (s != NDT_OK) return s;
   ctx->last_n = n_orbits;
@@ -727,6 +759,12 @@ ndt_status ndt_set_launch(ndt_ctx* ctx, int32_t mode, int32_t orbit_tile, int32_
   }
   ctx->mode = mode;
   ctx->use_graph = use_graph ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_set_offchip_test(ndt_ctx* ctx, int32_t enabled) {
+  if (!ctx) return NDT_EINVAL;
+  ctx->offchip = enabled ? 1 : 0;
   return NDT_OK;
 }
 
@@ -963,9 +1001,10 @@ ndt_status ndt_get_stats(ndt_ctx* ctx, ndt_stats* out) {
   NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
   std::memset(out, 0, sizeof *out);
-  unsigned long long cnt[2];
-  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 16, cudaMemcpyDeviceToHost), "counters");
+  unsigned long long cnt[4];
+  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 32, cudaMemcpyDeviceToHost), "counters");
   out->kernel_launches = ctx->launches;
+  out->offchip_skipped = (int64_t)cnt[3];
   out->samples = ctx->samples;
   out->valid_samples = (int64_t)cnt[0];
   out->kepler_failures = (int64_t)cnt[1];

@@ -46,11 +46,22 @@ struct Walk {
   OrbitConst oc;
   CSum sp, sf;
   int cnt;
+  int skipped;         // samples whose FP64 work the off-chip test removed
   bool failed;
+  float rf[3], vf[3], tf;   // FP32 copy of the state and its epoch (off-chip test)
 };
 
+__device__ __forceinline__ void walk_fp32_copy(Walk& w, float tf) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    w.rf[i] = d2f_trunc(w.r[i]);
+    w.vf[i] = d2f_trunc(w.v[i]);
+  }
+  w.tf = tf;
+}
+
 __device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double* __restrict__ states,
-                                          int64_t n, int64_t o, double t0) {
+                                          int64_t n, int64_t o, double t0, double t_ref = 0.0) {
   load_state(states, n, o, w.r, w.v);
   w.rn = sqrt(w.r[0] * w.r[0] + w.r[1] * w.r[1] + w.r[2] * w.r[2]);
   w.inv_r = 1.0 / w.rn;
@@ -59,10 +70,23 @@ __device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double*
   w.sp = CSum{0.0f, 0.0f};
   w.sf = CSum{0.0f, 0.0f};
   w.cnt = 0;
+  w.skipped = 0;
   w.failed = false;
+  walk_fp32_copy(w, (float)(t0 - t_ref));
 }
 
-template <int PT>
+// Persistent form: before the FP64 step, the warp skips the sample when the
+// FP32 off-chip test holds for every lane (lanes without work vote yes); the
+// state then stays at its last epoch and the next computed step is longer.
+// Every lane of the warp must call this (the vote is warp-wide).
+__device__ __forceinline__ bool warp_skips(Walk& w, const Phys& ph, const ExpDev& e, bool active) {
+  const bool off = !active || w.failed || certainly_off_chip(ph, w.oc, w.rf, w.vf, w.tf, e);
+  if (!__all_sync(0xffffffffu, off)) return false;
+  if (active && !w.failed) w.skipped += 1;
+  return true;
+}
+
+template <int PT, bool FP32_COPY = false>
 __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDev& e,
                                             const void* __restrict__ planes) {
   if (w.failed) return;
@@ -72,6 +96,7 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
     return;
   }
   w.t_prev = e.t;
+  if (FP32_COPY) walk_fp32_copy(w, e.tf);
   double rho[3], x, y;
   apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
   int ix, iy;
@@ -85,7 +110,7 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
 
 __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, int64_t o,
                                             bool active) {
-  int valid = 0, fails = 0;
+  int valid = 0, fails = 0, skipped = 0;
   if (active) {
     const float P = w.sp.value(), F = w.sf.value();
     if (a.psi_sum) a.psi_sum[o] = P;
@@ -97,14 +122,17 @@ __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, i
     a.snr[o] = nu;
     valid = w.cnt;
     fails = w.failed ? 1 : 0;
+    skipped = w.skipped;
   }
   for (int off = 16; off > 0; off >>= 1) {
     valid += __shfl_xor_sync(0xffffffffu, valid, off);
     fails += __shfl_xor_sync(0xffffffffu, fails, off);
+    skipped += __shfl_xor_sync(0xffffffffu, skipped, off);
   }
   if ((threadIdx.x & 31) == 0 && a.counters) {
     if (valid) atomicAdd(a.counters + 0, (unsigned long long)valid);
     if (fails) atomicAdd(a.counters + 1, (unsigned long long)fails);
+    if (skipped) atomicAdd(a.counters + 3, (unsigned long long)skipped);
   }
 }
 
@@ -164,19 +192,28 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
     const bool active = o < o_end;
     const int64_t e_begin = __ldg(a.fam_exp_off + f), e_end = __ldg(a.fam_exp_off + f + 1);
     Walk w;
-    if (active) walk_init(w, a.ph, a.states, a.n, o, a.t0);
+    if (active) {
+      walk_init(w, a.ph, a.states, a.n, o, a.t0, a.t_ref);
+    } else {
+      w.failed = true;   // no orbit: votes "off-chip" and does no work
+    }
+    constexpr int kWords = (int)(sizeof(ExpDev) / 8);
     for (int64_t eb = e_begin; eb < e_end; eb += ET) {
       const int cnt = (int)min((int64_t)ET, e_end - eb);
-      // stage cnt exposure records (19 doubles each) into shared memory
+      // stage cnt exposure records (kWords 8-byte words each) into shared memory
       double* dst = reinterpret_cast<double*>(&stage[team][0]);
-      for (int i = tl; i < cnt * 19; i += TEAM) {
-        const int jj = i / 19, wd = i % 19;
+      for (int i = tl; i < cnt * kWords; i += TEAM) {
+        const int jj = i / kWords, wd = i % kWords;
         const int j = __ldg(a.fam_exp_pos + eb + jj);
         dst[i] = __ldg(reinterpret_cast<const double*>(a.ex + j) + wd);
       }
       team_sync(team, TEAM);
-      if (active)
-        for (int jj = 0; jj < cnt; ++jj) walk_sample<PT>(w, a.ph, stage[team][jj], a.planes);
+      // every lane runs the loop: the off-chip vote is warp-wide
+      for (int jj = 0; jj < cnt; ++jj) {
+        const ExpDev& e = stage[team][jj];
+        if (a.offchip_test && warp_skips(w, a.ph, e, active)) continue;
+        walk_sample<PT, true>(w, a.ph, e, a.planes);
+      }
       team_sync(team, TEAM);
     }
     walk_finish(w, a, o, active);

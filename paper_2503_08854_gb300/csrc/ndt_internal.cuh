@@ -35,8 +35,14 @@ struct ExpDev {
   float s_psi;       // dequantisation scale of psi (1 for FP32 planes)
   float s_phi;       // dequantisation scale of phi
   int32_t pad_;
+  // FP32 copies for the off-chip test of the persistent form
+  float tf;          // epoch - t_ref (days), t_ref = earliest exposure epoch
+  float obs_f[3], p0_f[3], ax_f[3], ay_f[3], crpix_f[2];
+  float ppr;         // largest pixel stretch per radian at the tangent point (||CD^-1|| in px/rad)
+  float cos_far;     // cos(largest off-axis angle of the chip + 0.01 rad), or -2 (never)
+  float pad2_;
 };
-static_assert(sizeof(ExpDev) == 152, "ExpDev layout");
+static_assert(sizeof(ExpDev) == 224 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
@@ -146,12 +152,21 @@ __device__ __forceinline__ void stumpff(double z, double& C, double& S) {
 }
 
 // Per-orbit constants of the two-body motion.
+// Products with these replace divisions by 6 and 24 (an FP64 division is a
+// multi-instruction sequence on the FP64 pipe); they only scale correction
+// terms, so their last-bit rounding does not matter.
+constexpr double kInv6 = 1.0 / 6.0;
+constexpr double kInv24 = 1.0 / 24.0;
+
 struct OrbitConst {
   double alpha;        // 2/r - v^2/GM (reciprocal semi-major axis), conserved
   double period;       // orbital period (bound orbits), else 0
   double inv_period;
   double half_period;  // steps longer than this are reduced modulo the period
   double series_dt;    // steps shorter than this use the truncated f/g series
+  // bounds along the whole conic for the off-chip test (FP32): |d^3 r/dt^3| / 6,
+  // GM / (2 q^2) >= |acceleration| / 2, and the perihelion speed v_q >= |v|
+  float jerk6, half_acc, vq;
 };
 
 __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
@@ -183,6 +198,22 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     const double vq2 = ph.gm * (2.0 / q - oc.alpha);
     const double K = ph.gm / (q * q * q) + vq2 / (q * q);
     oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
+    // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
+    // <= 4 GM v_q / q^3 anywhere on the conic (r >= q, |v| <= v_q).
+    if (ph.force_free) {
+      oc.jerk6 = 0.0f;
+      oc.half_acc = 0.0f;
+      oc.vq = (float)sqrt(v2);
+    } else if (q > 0.0 && vq2 >= 0.0 && K < 1e300) {
+      const double vq = sqrt(vq2);
+      oc.jerk6 = (float)(4.0 * ph.gm * vq / (q * q * q) * kInv6);
+      oc.half_acc = (float)(0.5 * ph.gm / (q * q));
+      oc.vq = (float)vq;
+    } else {
+      oc.jerk6 = INFINITY;   // degenerate conic: never declared off-chip
+      oc.half_acc = INFINITY;
+      oc.vq = INFINITY;
+    }
   }
   return oc;
 }
@@ -205,11 +236,6 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
 // takes two Newton steps y <- y (3 - x y^2)/2 (error ~ (3/2) e^2 per step,
 // so below 1e-20 after two).
 // ---------------------------------------------------------------------------
-// Products with these replace divisions by 6 and 24 (an FP64 division is a
-// multi-instruction sequence on the FP64 pipe); they only scale correction
-// terms, so their last-bit rounding does not matter.
-constexpr double kInv6 = 1.0 / 6.0;
-constexpr double kInv24 = 1.0 / 24.0;
 
 __device__ __forceinline__ void fg_series_step(const Phys& ph, double t, double r[3], double v[3],
                                                double& rn, double& inv_r) {
@@ -370,6 +396,69 @@ __device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double x, double 
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
 }
 
+// FP64 -> FP32 by truncation on the integer pipe (exponent rebias and
+// mantissa shift of the IEEE-754 bit patterns), so the FP64 pipe that bounds
+// the stacking kernel does no conversions for the off-chip test.  Relative
+// error < 2^-23; magnitudes below 2^-126 become 0, above FP32 range infinity.
+__device__ __forceinline__ float d2f_trunc(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (ex <= 0) return __uint_as_float(sign);
+  if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)ex << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// Off-chip test of the persistent form (FP32, no FP64 instruction).  From the
+// state (r, v) at epoch t_prev (FP32 copies of the FP64 state), the position
+// at the exposure epoch is predicted to second order, p = r + v dt + a dt^2/2,
+// with the light time to first order.  The Taylor remainder is at most
+// jerk6 |dt|^3 (jerk6 bounds |d^3r/dt^3| / 6 on the whole conic); the light-
+// time expansion adds at most half_acc tau^2, FP32 rounding of the inputs and
+// sums < 1e-6 (|r| + |rho| + v_q |dt|), the FP32 epochs v_q * 1e-4 d.  The
+// position error E becomes an angle below E / (|rho| - E), and within 45 deg
+// of the tangent point the TAN projection stretches angles by at most
+// sec^2 = 2 times ||CD^-1||: the sample is declared off-chip when the
+// predicted pixel lies outside the image by more than 2.5 times that bound
+// plus 2 px.  Farther out, with an angular error below 0.005 rad, it is
+// declared off-chip when its off-axis angle exceeds the chip's largest one
+// (a corner) by more than 0.01 rad.  A false "off-chip" would need the bounds
+// above to fail; the test never fires for degenerate conics (infinite
+// bounds) or NaNs.
+__device__ __forceinline__ bool certainly_off_chip(const Phys& ph, const OrbitConst& oc,
+                                                   const float rf[3], const float vf[3], float tf,
+                                                   const ExpDev& e) {
+  const float dt = e.tf - tf;
+  const float r2 = rf[0] * rf[0] + rf[1] * rf[1] + rf[2] * rf[2];
+  const float ir = rsqrtf(r2);
+  const float k = -ph.gm_f * ir * ir * ir;
+  float rho[3], vj[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float acc = k * rf[i];
+    rho[i] = fmaf(0.5f * acc, dt * dt, fmaf(vf[i], dt, rf[i])) - e.obs_f[i];
+    vj[i] = fmaf(acc, dt, vf[i]);
+  }
+  const float rr2 = rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2];
+  const float rr = rr2 * rsqrtf(rr2);   // NaN for rho = 0: the test then declines
+  const float tau = rr * ph.inv_c;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rho[i] = fmaf(-vj[i], tau, rho[i]);
+  const float adt = fabsf(dt);
+  const float err = oc.jerk6 * adt * adt * adt + oc.half_acc * tau * tau +
+                    1e-6f * (r2 * ir + rr) + oc.vq * fmaf(1e-6f, adt, 1e-4f);
+  const float den = rho[0] * e.p0_f[0] + rho[1] * e.p0_f[1] + rho[2] * e.p0_f[2];
+  if (!(rr > 2.0f * err)) return false;
+  // fast intrinsics (a few ulp): their error is far inside the 1e-6 slack
+  const float eps = __fdividef(err, rr - err);       // angular error bound (rad)
+  // (0.005 rad of the 0.01 rad angle margin is left for FP32 rounding of den / rr)
+  if (!(den > 0.70710678f * rr)) return eps <= 0.005f && den < e.cos_far * rr;
+  const float m = fmaf(2.5f * e.ppr, eps, 2.0f);
+  const float x = e.crpix_f[0] + __fdividef(rho[0] * e.ax_f[0] + rho[1] * e.ax_f[1] + rho[2] * e.ax_f[2], den);
+  const float y = e.crpix_f[1] + __fdividef(rho[0] * e.ay_f[0] + rho[1] * e.ay_f[1] + rho[2] * e.ay_f[2], den);
+  return x < -0.5f - m || x > (float)e.W - 0.5f + m || y < -0.5f - m || y > (float)e.H - 0.5f + m;
+}
+
 template <int PT>
 __device__ __forceinline__ float2 gather_plane(const void* __restrict__ planes, const ExpDev& e,
                                                int ix, int iy) {
@@ -437,8 +526,10 @@ struct StackArgs {
   int32_t* nobs;
   float* snr;
   int32_t min_obs;
-  unsigned long long* counters;  // [0] valid samples, [1] Kepler failures
+  unsigned long long* counters;  // [0] valid samples, [1] Kepler failures, [3] skipped warp-samples
   Phys ph;
+  double t_ref;                // epoch origin of ExpDev::tf
+  int32_t offchip_test;        // persistent form: skip FP64 work of certainly off-chip samples
 };
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);

@@ -39,7 +39,8 @@ class Stats(C.Structure):
                 ("valid_samples", C.c_int64), ("kepler_failures", C.c_int64),
                 ("last_stack_ms", C.c_float), ("last_planes_ms", C.c_float),
                 ("last_topk_ms", C.c_float), ("orbit_tile", C.c_int32), ("exp_tile", C.c_int32),
-                ("launch_mode", C.c_int32), ("plane_dtype", C.c_int32)]
+                ("launch_mode", C.c_int32), ("plane_dtype", C.c_int32),
+                ("offchip_skipped", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -60,6 +61,7 @@ _lib.ndt_topk_candidates.argtypes = [_vp, _i64, _vp, _vp, C.POINTER(_i64)]
 _lib.ndt_predict_positions.argtypes = [_vp, _vp, _f64, _i64, _vp]
 _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
+_lib.ndt_set_offchip_test.argtypes = [_vp, _i32]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
 _lib.ndt_get_stats.argtypes = [_vp, C.POINTER(Stats)]
 _lib.ndt_stamps.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, _vp, _vp]
@@ -191,6 +193,10 @@ def set_launch(ctx, mode, orbit_tile=64, exp_tile=16, use_graph=False):
     _check(ctx, _lib.ndt_set_launch(ctx, int(mode), int(orbit_tile), int(exp_tile), int(bool(use_graph))))
 
 
+def set_offchip_test(ctx, enabled):
+    _check(ctx, _lib.ndt_set_offchip_test(ctx, int(bool(enabled))))
+
+
 def autotune(ctx, states_soa, t0, n_orbits, families=None, times_ms=None):
     if families is None:
         fo = fe = fi = None
@@ -260,7 +266,8 @@ def exported_symbols():
     """Names of the C entry points this binding uses (all must be exported)."""
     return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
             "ndt_load_exposures", "ndt_stack_orbits", "ndt_topk_candidates",
-            "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_autotune",
+            "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_set_offchip_test",
+            "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_topk_noalloc"]

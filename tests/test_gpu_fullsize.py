@@ -88,6 +88,26 @@ def test_mba_full_size_sampled(gpu, form):
     assert np.abs(xy[fin] - rx[fin]).max() <= POS_TOL
 
 
+@pytest.mark.parametrize("workload", ["mba", "batched"])
+def test_full_size_forms_count_the_same_samples(gpu, workload):
+    """Every orbit of the full workload: the plain form (every sample computed
+    in FP64) and the persistent form (off-chip test on, BF16 planes) find the
+    same in-bounds exposures for every orbit, while the persistent form skips
+    the FP64 work of a large share of the off-chip samples."""
+    sky = synth.mba_sky() if workload == "mba" else synth.batched_sky()
+    fam = None if workload == "mba" else sky.families
+    imgs = _device_sky(gpu, sky)
+    plain = _stack_all(gpu, sky, imgs, "f32", "plain", families=fam)
+    st_plain = gpu.stats()
+    pers = _stack_all(gpu, sky, imgs, "bf16", "persistent", families=fam)
+    st = gpu.stats()
+    assert st["valid_samples"] == st_plain["valid_samples"]
+    assert torch.equal(plain["nobs"], pers["nobs"])
+    off_chip = st["samples"] - st["valid_samples"]
+    assert st["offchip_skipped"] <= off_chip
+    assert st["offchip_skipped"] >= 0.5 * off_chip, (st["offchip_skipped"], off_chip)
+
+
 def test_batched_uneven_full_size_sampled(gpu):
     """4,096 families x 16,384 orbits (NEO, MBA, KBO), 20-400 of 400 exposures
     of 2048^2 each, FP32 planes, persistent work queue under a CUDA graph."""

@@ -252,6 +252,38 @@ def test_every_persistent_tile_shape(gpu, ot, et):
     check_stack(out, O.stack(sky.states, sky.t0, sky.ex, images=list(imgs)))
 
 
+def test_offchip_test_changes_no_result(gpu):
+    """The persistent form's off-chip test removes FP64 work without changing
+    what is stacked: on an MBA-shaped sky whose chips cover 60-100 % of the
+    population, the sums with the test on equal those with it off, the
+    plain form's sample count and the oracle's sums, and samples were
+    skipped."""
+    sky = synth.mba_sky(n_exp=40, nights=6, size=512, n_true=24, fam_size=256,
+                        scale_arcsec=10.5 * 4096 / 512)
+    imgs = synth.noise_images(sky.ex, sky.seed)
+    gpu.load(sky.ex, imgs)
+    plain = gpu.stack(sky.states, sky.t0)
+    valid_plain = gpu.stats()["valid_samples"]
+    ndt.set_launch(gpu.ctx, ndt.LAUNCH_PERSISTENT, 64, 16)
+    ndt.set_offchip_test(gpu.ctx, False)
+    off = gpu.stack(sky.states, sky.t0)
+    assert gpu.stats()["offchip_skipped"] == 0
+    ndt.set_offchip_test(gpu.ctx, True)
+    on = gpu.stack(sky.states, sky.t0)
+    st = gpu.stats()
+    assert st["valid_samples"] == valid_plain < st["samples"]
+    assert st["offchip_skipped"] >= 0.05 * st["samples"], st
+    assert st["offchip_skipped"] <= st["samples"] - st["valid_samples"]
+    for other in (off, plain):
+        assert np.array_equal(on["nobs"], other["nobs"])
+        scale = np.sqrt(np.maximum(on["phi"], 1e-30))
+        assert np.all(np.abs(on["psi"] - other["psi"]) <= 1e-6 * np.maximum(1.0, scale))
+        assert np.allclose(on["phi"], other["phi"], rtol=1e-6, atol=0)
+    sel = np.sort(np.random.default_rng(3).choice(len(sky.states), 256, replace=False))
+    ref = O.stack(sky.states[sel], sky.t0, sky.ex, images=list(imgs))
+    check_stack({k: v[sel] for k, v in on.items()}, ref)
+
+
 def test_host_pointers_give_device_results(gpu):
     sky = _ragged_sky()
     imgs = _images(sky)

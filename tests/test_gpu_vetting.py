@@ -76,15 +76,16 @@ def _params(seed):
 
 
 def test_cnn_forward_matches_oracle(gpu):
-    """The tensor-core forward computes the BF16-weight, BF16-activation network:
-    it matches the oracle's variant with the same roundings (differences only
-    from FP32 vs FP64 accumulation and the rare BF16 rounding flip they cause),
-    and stays within BF16 rounding of the full-precision network."""
+    """The tensor-core forward computes the network with BF16 weights and BF16
+    activations: it matches the oracle's variant with the same roundings
+    (differences only from FP32 vs FP64 accumulation and the rare BF16
+    rounding flip they cause), and stays within BF16 rounding of the
+    full-precision network."""
     xb, x64 = _bf16_batch(1, 300)                 # several stamps per CTA
     th = _params(2)
     p = torch.as_tensor(th, dtype=torch.float32, device=gpu.dev)
     th32 = th.astype(np.float32).astype(np.float64)
-    ref = V.forward(th32, x64, bf16_hidden=True)
+    ref = V.forward(th32, x64, bf16_operands=True)
     z = vetting.logits(gpu.ctx, p, xb.to(gpu.dev)).cpu().numpy()
     scale = np.abs(ref).max()
     np.testing.assert_allclose(z, ref, rtol=2e-3, atol=2e-3 * scale)
