@@ -40,7 +40,9 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # off-chip test removed), and the FP64-pipe thread instructions per computed
 # sample (conversions and compares included).  MBA: workload at 512 orbits per
 # family and 1024 x 1024 images; batched: 128 families and 512 x 512 images.
-FP64_PER_SAMPLE = {"mba": (143.6, 110.6), "batched": (147.9, 114.7)}
+# MBA: 8.636e7 computed samples, 48.48 DFMA + 39.48 DMUL + 8.33 DADD each;
+# batched: 2.037e8 computed samples, 54.74 DFMA + 38.05 DMUL + 7.78 DADD.
+FP64_PER_SAMPLE = {"mba": (144.8, 111.9), "batched": (155.3, 120.6)}
 # DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
 # measured on the current kernel.
 TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
@@ -69,6 +71,8 @@ def parse():
     p.add_argument("--tiles", default=None, help="fixed OT,ET for the persistent form (no autotune)")
     p.add_argument("--no-vet", action="store_true", help="skip the CNN vetting stage")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
+    p.add_argument("--vet-batch", type=int, default=1 << 20,
+                   help="candidates of the separately timed vetting pass (0: skip)")
     a = p.parse_args()
     if a.size is None:
         a.size = 2048 if a.workload == "batched" else 4096
@@ -307,12 +311,40 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
                    recall_topk=rec,
                    planes_ms=stats["last_planes_ms"], topk_ms=stats["last_topk_ms"], tiles=tiles,
                    top_snr=float(val[0].item()))
+        if vet is not None and args.vet_batch > 0:
+            out["vet_batch"] = vet_batch_rate(args, ctx, stream, sky, states, vet_params, device)
         e2e = None
         if not args.no_e2e and form.name == "chosen":
             e2e = bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device)
         return out, e2e
     finally:
         ndt.destroy(ctx)
+
+
+def vet_batch_rate(args, ctx, stream, sky, states, vet_params, device):
+    """Vetting throughput at the learned-vetting workload's scale: the top
+    ``--vet-batch`` candidates of the stacked batch (ranked once, untimed)
+    get stamps and CNN scores; CUDA events time that call alone."""
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    n = states.shape[1]
+    m = min(args.vet_batch, n)
+    idx = torch.empty(m, dtype=torch.int64, device=device)
+    ndt.topk_candidates(ctx, m, idx)
+    scores = torch.empty(m, device=device)
+    ndt.vet(ctx, vet_params, states, sky.t0, n, idx, scores)     # warm-up
+    ms = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ndt.vet(ctx, vet_params, states, sky.t0, n, idx, scores)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.mean(ms)
+    return {"candidates": m, "ms": t, "vetted_candidates_per_s": m / (t / 1e3),
+            "exposures": int(sky.ex.n)}
 
 
 def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
@@ -500,6 +532,8 @@ def main():
         vet_info["vet_ms_per_step"] = statistics.mean(r["vet_ms"])
         vet_info["vetted_candidates_per_s"] = min(args.k, states.shape[1]) / (
             statistics.mean(r["vet_ms"]) / 1e3)
+        if r.get("vet_batch"):
+            vet_info["batch"] = r["vet_batch"]
         line["vetting"] = vet_info
     for name, res in results.items():
         s = statistics.mean(res["step_ms"]) / 1e3
