@@ -22,12 +22,15 @@
 //     x 16 bytes), 13 steps with a zero-weight 26th tap.
 //   * The weights of all three layers sit in shared memory as BF16 B
 //     operands (N = 32 output channels x 16 K per step, 1 KB per step).
-//   * One thread issues a layer's MMAs (5 tiles x 13 or 50 steps, M = 128,
+//   * Lane 0 of warp t issues the MMAs of tile t (13 or 50 K-steps, M = 128,
 //     N = 32, K = 16, BF16 x BF16 -> FP32 in TMEM) back to back and commits
-//     once to an mbarrier; four warps then read the accumulators with
+//     them to the layer's mbarrier (five issuers: a single thread's issue
+//     rate, not the tensor core, would bound these small MMAs); four warps
+//     then read the accumulators with
 //     tcgen05.ld, add the bias, apply ReLU and write the next layer's BF16
-//     chunk planes (or pool, after layer 3).  Every wait is bounded and
-//     records a timeout instead of hanging.
+//     chunk planes (or pool, after layer 3, by a warp transpose-reduce into
+//     per-warp channel sums).  Every wait is bounded and records a timeout
+//     instead of hanging.
 // Precision: BF16 stamps, BF16 weights, BF16 activations between layers,
 // FP32 accumulation; pooling, head and bias in FP32.
 #include <cuda_bf16.h>
@@ -48,7 +51,7 @@ constexpr int MTILES = 5;                      // 5 x 128 rows >= 525 = 21 x 25
 constexpr int NPP = 768;                       // pixels per chunk plane
 constexpr int KS1 = 13;                        // layer-1 K-steps (26 tap slots)
 constexpr int KS2 = CH * KK / 16;              // 50 K-steps of layers 2 and 3
-constexpr int kThreadsTC = 160;                // 4 epilogue warps + 1 MMA warp
+constexpr int kThreadsTC = 160;                // 5 warps: MMA issue per tile, 4 do the epilogue
 constexpr uint32_t kTmemCols = 256;            // 5 x 32 accumulator columns, power of 2
 
 // shared-memory map (bytes from a 128-aligned base)
@@ -59,8 +62,8 @@ constexpr int O_ACT1 = O_ACT0 + 4 * CHB;       // layer-2 output: 4 chunk planes
 constexpr int O_W1 = O_ACT1 + 4 * CHB;         // 13 K-steps x 1 KB
 constexpr int O_W2 = O_W1 + KS1 * 1024;        // 50 K-steps x 1 KB
 constexpr int O_W3 = O_W2 + KS2 * 1024;
-constexpr int O_B = O_W3 + KS2 * 1024;         // FP32 b1 | b2 | b3 | wl | pooled: 5 x 32
-constexpr int O_BAR = O_B + 5 * 32 * 4;        // one mbarrier (layer done)
+constexpr int O_B = O_W3 + KS2 * 1024;         // FP32 b1 | b2 | b3 | wl: 4 x 32, pooled: 4 warps x 32
+constexpr int O_BAR = O_B + 8 * 32 * 4;        // one mbarrier (layer done)
 constexpr int O_MISC = O_BAR + 8;              // tmem slot, abort flag
 constexpr int SMEM_USED = O_MISC + 16;
 constexpr size_t kSmemTC = SMEM_USED + 128;    // + base alignment slack
@@ -69,6 +72,7 @@ static_assert(O_W1 % 1024 == 0 && O_W2 % 1024 == 0 && O_W3 % 1024 == 0, "operand
 static_assert(O_B % 16 == 0 && O_BAR % 8 == 0 && O_MISC % 4 == 0, "alignment");
 static_assert(kSmemTC <= 232448, "shared memory of one CTA");
 static_assert(CHB / 16 < (1 << 14), "LBO field");
+static_assert(MTILES == kThreadsTC / 32, "warp t issues the MMAs of tile t");
 // The farthest pixel a tile row reads: m <= 639 plus the largest tap shift,
 // 125 pixels for the zero-weight 26th tap of layer 1 (104 for real taps).
 static_assert(MTILES * 128 - 1 + 5 * SP < NPP, "chunk plane covers every shifted row");
@@ -101,8 +105,8 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
   uint8_t* in_plane = sm + O_IN;
   uint8_t* act[2] = {sm + O_ACT0, sm + O_ACT1};
-  float* bias = reinterpret_cast<float*>(sm + O_B);        // b1 | b2 | b3 | wl | pooled
-  float* pooled = bias + 4 * 32;
+  float* bias = reinterpret_cast<float*>(sm + O_B);        // b1 | b2 | b3 | wl
+  float* pooled = bias + 4 * 32;                           // per-warp channel sums [4][32]
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + O_BAR);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + O_MISC);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + O_MISC + 4);
@@ -132,10 +136,9 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     bias[32 + tid] = th[OB2 + tid];
     bias[64 + tid] = th[OB3 + tid];
     bias[96 + tid] = th[OWL + tid];
-    pooled[tid] = 0.0f;
   }
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
+    tc::mbar_init(&bar[0], MTILES);   // one commit per issuing thread and layer
     tc::fence_mbar_init();
     *abort_flag = 0;
   }
@@ -148,47 +151,53 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
   const float bl = th[OBL];
   uint32_t phase = 0;
 
-  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
-    // ---- stamp -> channels 0 and 1 of the layer-1 input chunk ---------------
+  // stamp b -> channels 0 and 1 of the layer-1 input chunk (threads 0-127)
+  auto load_input = [&](int64_t b) {
     const __nv_bfloat16* xs = x + b * 2 * NPIX;
-    for (int p = tid; p < NPIX; p += kThreadsTC) {
+    for (int p = tid; p < NPIX; p += 128) {
       const uint32_t v = (uint32_t)__bfloat16_as_ushort(xs[p]) |
                          ((uint32_t)__bfloat16_as_ushort(xs[NPIX + p]) << 16);
       *reinterpret_cast<uint32_t*>(in_plane + pad_q(p / S, p % S) * 16) = v;
     }
-    tc::fence_proxy_async_smem();
-    tc::tc_fence_before_sync();
-    __syncthreads();
-    tc::tc_fence_after_sync();
+  };
+  if (warp < 4 && blockIdx.x < n) load_input(blockIdx.x);
+  tc::fence_proxy_async_smem();
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
 
+  for (int64_t b = blockIdx.x; b < n; b += gridDim.x) {
     for (int L = 0; L < 3; ++L) {
-      // ---- MMA issue: one thread, all K-steps of all tiles, one commit -----
-      if (warp == 4 && lane == 0 && !*abort_flag) {
+      // ---- MMA issue: lane 0 of warp t issues every K-step of tile t and -----
+      // commits them (five issuers: one thread's issue rate would bound the
+      // N = 32 MMAs well below the shared-memory operand rate)
+      if (lane == 0 && !*abort_flag) {
+        const int t = warp;
         if (L == 0) {
-          const uint32_t a0 = tc::smem_addr(in_plane), w0 = tc::smem_addr(sm + O_W1);
+          const uint32_t a0 = tc::smem_addr(in_plane) + t * 128 * 16, w0 = tc::smem_addr(sm + O_W1);
+#pragma unroll 1
           for (int s = 0; s < KS1; ++s) {
             const int sh0 = tap_shift(2 * s), sh1 = tap_shift(2 * s + 1);
-            const uint64_t bd = tc::smem_desc(w0 + s * 1024, 512, 128);
-#pragma unroll
-            for (int t = 0; t < MTILES; ++t)
-              tc::mma_bf16(tmem + 32 * t, tc::smem_desc(a0 + (t * 128 + sh0) * 16, (sh1 - sh0) * 16, 128),
-                           bd, kIdesc, s > 0);
+            tc::mma_bf16(tmem + 32 * t, tc::smem_desc(a0 + sh0 * 16, (sh1 - sh0) * 16, 128),
+                         tc::smem_desc(w0 + s * 1024, 512, 128), kIdesc, s > 0);
           }
         } else {
-          const uint32_t a0 = tc::smem_addr(act[L - 1]), w0 = tc::smem_addr(sm + (L == 1 ? O_W2 : O_W3));
+          const uint32_t a0 = tc::smem_addr(act[L - 1]) + t * 128 * 16;
+          const uint32_t w0 = tc::smem_addr(sm + (L == 1 ? O_W2 : O_W3));
+#pragma unroll 2
           for (int s = 0; s < KS2; ++s) {
             const int sh = tap_shift(s >> 1), g = s & 1;
-            const uint64_t bd = tc::smem_desc(w0 + s * 1024, 512, 128);
-#pragma unroll
-            for (int t = 0; t < MTILES; ++t)
-              tc::mma_bf16(tmem + 32 * t, tc::smem_desc(a0 + 2 * g * CHB + (t * 128 + sh) * 16, CHB, 128),
-                           bd, kIdesc, s > 0);
+            tc::mma_bf16(tmem + 32 * t, tc::smem_desc(a0 + 2 * g * CHB + sh * 16, CHB, 128),
+                         tc::smem_desc(w0 + s * 1024, 512, 128), kIdesc, s > 0);
           }
         }
         tc::mma_commit(&bar[0]);
       }
       // ---- epilogue: TMEM -> bias, ReLU -> next chunk planes or the pool ----
       if (warp < 4) {
+        // the input plane is read only by layer-1 MMAs: stage the next stamp
+        // while layer 3 runs on the tensor core
+        if (L == 2 && b + gridDim.x < n) load_input(b + gridDim.x);
         if (!*abort_flag && !tc::mbar_wait_bounded(&bar[0], phase & 1, kWaitLimit)) *abort_flag = 1;
         tc::tc_fence_after_sync();
         const float* bL = bias + 32 * L;
@@ -219,12 +228,20 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
           }
         }
         if (L == 2) {
+          // transpose-reduce over the warp: each round hands half of the
+          // remaining channels to the partner lane, so after 16+8+4+2+1
+          // shuffles lane o holds the warp's sum of channel o
 #pragma unroll
-          for (int o = 0; o < 32; ++o) {
-            float s2 = pool[o];
-            for (int off = 16; off > 0; off >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, off);
-            if (lane == 0) atomicAdd(&pooled[o], s2);
+          for (int h = 16; h >= 1; h >>= 1) {
+            const bool upper = (lane & h) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+              const float give = upper ? pool[i] : pool[i + h];
+              const float keep = upper ? pool[i + h] : pool[i];
+              pool[i] = keep + __shfl_xor_sync(0xffffffffu, give, h);
+            }
           }
+          pooled[warp * 32 + lane] = pool[0];
         }
       }
       ++phase;
@@ -235,22 +252,21 @@ __global__ void __launch_bounds__(kThreadsTC, 1)
     }
     // ---- head: logit = wl . mean(a3) + bl -----------------------------------
     if (tid < 32) {
-      float z = pooled[tid] * (1.0f / NPIX) * bias[96 + tid];
-      pooled[tid] = 0.0f;
+      const float g = (pooled[tid] + pooled[32 + tid]) + (pooled[64 + tid] + pooled[96 + tid]);
+      float z = g * (1.0f / NPIX) * bias[96 + tid];
       for (int off = 16; off > 0; off >>= 1) z += __shfl_xor_sync(0xffffffffu, z, off);
       if (tid == 0) logits[b] = *abort_flag ? __int_as_float(0x7fc00000) : z + bl;
     }
   }
   // ---- teardown: every MMA of this CTA has completed before TMEM is freed ----
-  if (warp == 4) {
-    if (lane == 0) {
-      tc::mma_commit(&bar[0]);
-      if (!tc::mbar_wait_bounded(&bar[0], phase & 1, kWaitLimit)) *abort_flag = 1;
-    }
-    __syncwarp();
-    tc::tc_fence_after_sync();
-    tc::tmem_dealloc(tmem, kTmemCols);
-  }
+  // (each issuer commits once more; the phase completes when all of their
+  // MMAs have, normally at once)
+  if (lane == 0) tc::mma_commit(&bar[0]);
+  if (tid == 0 && !tc::mbar_wait_bounded(&bar[0], phase & 1, kWaitLimit)) *abort_flag = 1;
+  tc::tc_fence_before_sync();
+  __syncthreads();
+  tc::tc_fence_after_sync();
+  if (warp == 4) tc::tmem_dealloc(tmem, kTmemCols);
   __syncthreads();
   if (tid == 0 && *abort_flag) atomicExch(err, 1);
 }

@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
                                                    int64_t n_cand, const ExpDev* __restrict__ ex,
                                                    int32_t n_exp, Phys ph, int2* __restrict__ pos,
                                                    unsigned long long* counters) {
-  const int64_t i = (int64_t)blockIdx.x * 128 + threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cand) return;
   const int64_t o = cand[i];
   int2* out = pos + i * n_exp;
@@ -83,6 +83,11 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
   }
 }
 
+// Exposures are taken kStampUnroll at a time: every thread issues the
+// gathers of all of them before accumulating (in exposure order), so several
+// independent loads are in flight per thread instead of one.
+constexpr int kStampUnroll = 4;
+
 template <int PT>
 __global__ void __launch_bounds__(kVetThreads) k_stamps(const int2* __restrict__ pos, int64_t n_cand,
                                                          const ExpDev* __restrict__ ex, int32_t n_exp,
@@ -94,22 +99,37 @@ __global__ void __launch_bounds__(kVetThreads) k_stamps(const int2* __restrict__
     int cnt[2] = {0, 0};
     for (int k = 0; k < 2; ++k) sp[k] = sf[k] = sq[k] = CSum{0.0f, 0.0f};
     const int p0 = threadIdx.x, p1 = threadIdx.x + kVetThreads;
-    for (int j = 0; j < n_exp; ++j) {
-      const int2 ctr = pos[c * n_exp + j];
-      if (ctr.x == INT_MIN) continue;
-      const ExpDev& e = ex[j];
+    const int2* cpos = pos + c * n_exp;
+    for (int j0 = 0; j0 < n_exp; j0 += kStampUnroll) {
+      float2 v[kStampUnroll][2];
+      bool ok[kStampUnroll][2];
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int p = k ? p1 : p0;
-        if (p >= NPIX) continue;
-        const int px = ctr.x + p % S - S / 2, py = ctr.y + p / S - S / 2;
-        if ((unsigned)px >= (unsigned)e.W || (unsigned)py >= (unsigned)e.H) continue;
-        const float2 v = gather_plane<PT>(planes, e, px, py);
-        if (!(v.y > 0.0f)) continue;
-        sp[k].add(v.x);
-        sf[k].add(v.y);
-        sq[k].add(__fdiv_rn(v.x * v.x, v.y));
-        cnt[k] += 1;
+      for (int u = 0; u < kStampUnroll; ++u) {
+        const int j = j0 + u;
+        const int2 ctr = j < n_exp ? cpos[j] : make_int2(INT_MIN, INT_MIN);
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int p = k ? p1 : p0;
+          ok[u][k] = false;
+          v[u][k] = make_float2(0.0f, 0.0f);
+          if (ctr.x == INT_MIN || p >= NPIX) continue;
+          const ExpDev& e = ex[j];
+          const int px = ctr.x + p % S - S / 2, py = ctr.y + p / S - S / 2;
+          if ((unsigned)px >= (unsigned)e.W || (unsigned)py >= (unsigned)e.H) continue;
+          v[u][k] = gather_plane<PT>(planes, e, px, py);
+          ok[u][k] = true;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kStampUnroll; ++u) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (!ok[u][k] || !(v[u][k].y > 0.0f)) continue;
+          sp[k].add(v[u][k].x);
+          sf[k].add(v[u][k].y);
+          sq[k].add(__fdividef(v[u][k].x * v[u][k].x, v[u][k].y));   // ~2 ulp
+          cnt[k] += 1;
+        }
       }
     }
 #pragma unroll
@@ -422,10 +442,13 @@ size_t cnn_smem_bytes() { return kCnnSmem; }
 cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, const int64_t* cand,
                                    int64_t n_cand, const ExpDev* ex, int32_t n_exp, Phys ph,
                                    int2* pos, unsigned long long* counters, cudaStream_t st) {
-  const int64_t blocks = (n_cand + 127) / 128;
+  // one warp per block while the candidates do not fill every SM with four
+  // 128-thread blocks, so that they spread over all SMs (FP64-bound threads)
+  const int threads = n_cand < 128 * 4 * 152 ? 32 : 128;
+  const int64_t blocks = (n_cand + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
-  k_stamp_pos<<<(unsigned)blocks, 128, 0, st>>>(states, n, t0, cand, n_cand, ex, n_exp, ph, pos,
-                                                counters);
+  k_stamp_pos<<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, cand, n_cand, ex, n_exp, ph, pos,
+                                                    counters);
   return cudaGetLastError();
 }
 
