@@ -292,9 +292,12 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
         barrier()
         torch.cuda.synchronize(device)
         t0 = time.perf_counter()
+        # NVTX range "timed_<form>": lets a profiler select exactly these launches
+        torch.cuda.nvtx.range_push(f"timed_{form.name}")
         step_ms, stack_ms, vet_ms = run_steps(ctx, stream, sky, imgs, states, k, args.steps, idx,
                                               val, form.plane, vet)
         torch.cuda.synchronize(device)
+        torch.cuda.nvtx.range_pop()
         wall = time.perf_counter() - t0
         stats = ndt.get_stats(ctx)
         launches = stats["kernel_launches"] - launches0
