@@ -43,9 +43,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # MBA: 8.636e7 computed samples, 48.48 DFMA + 39.48 DMUL + 8.33 DADD each;
 # batched: 2.037e8 computed samples, 54.74 DFMA + 38.05 DMUL + 7.78 DADD.
 FP64_PER_SAMPLE = {"mba": (144.8, 111.9), "batched": (155.3, 120.6)}
-# DRAM bytes (read + write) of one full-size stack launch, from ncu; None until
-# measured on the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
+# DRAM bytes (read + write) of one full-size persistent stack launch (BF16
+# planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
+# in a one-pass capture: MBA 1.86 GB + 72.1 MB, batched 3.54 GB + 274.7 MB.
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.932e9, "batched": 3.815e9}
 
 
 def parse():

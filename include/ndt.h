@@ -264,6 +264,28 @@ ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, flo
                              int64_t n_params, int32_t step, float lr, float beta1, float beta2,
                              float eps);
 
+/*
+ * trim_candidates: outlier trimming of candidates' intersections (paper
+ * sec. 5.2.3 removes intersections whose SNR is anomalously high compared
+ * with the expectation, by sigma clipping, and recomputes the stacked SNR).
+ * For each candidate cand_idx[i] (an index into the orbit batch `states`, SoA
+ * 6 x n_orbits as in stack_orbits, host or device), its valid intersections
+ * j (nearest pixel inside the image, phi_j > 0) are clipped by the rule
+ *   a = sum_K psi / sum_K phi,  r_j = psi_j / sqrt(phi_j) - a sqrt(phi_j),
+ *   K' = { j : r_j <= kappa },  repeated from K = all valid until K' == K or
+ *   max_iter rounds,
+ * and nu_out[i] = sum_K psi / sqrt(sum_K phi) (-inf if the sum of phi is 0
+ * or |K| < min_obs), nkept_out[i] = |K| (nkept_out may be NULL).  Outputs
+ * n_cand FP32 / int32 values, host or device memory, caller-owned.
+ * Indices outside [0, n_orbits) give -inf and 0.  kappa > 0 (INFINITY
+ * keeps every intersection), 1 <= max_iter <= 1000, min_obs >= 0; else
+ * NDT_EINVAL.  Uses the planes of the last load_exposures (NDT_ESTATE if
+ * none).  Synchronous.
+ */
+ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
+                               const int64_t *cand_idx, int64_t n_cand, float kappa, int32_t max_iter,
+                               int32_t min_obs, float *nu_out, int32_t *nkept_out);
+
 /* vet: stamps of the candidates (as ndt_stamps) scored by the network:
    scores[i] = sigmoid(logit) in [0, 1]. */
 ndt_status ndt_vet(ndt_ctx *ctx, const float *params, const double *states, double t0,

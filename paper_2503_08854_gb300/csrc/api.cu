@@ -71,7 +71,7 @@ struct ndt_ctx {
   DevBuf topk_scratch, topk_out;
   // vetting
   DevBuf cand_stage, stamp_pos, stamp_f32, stamp_bf16, cnn_x, cnn_labels, cnn_out, cnn_scratch,
-      cnn_params, cnn_grad;
+      cnn_params, cnn_grad, trim_bits, trim_nu, trim_n;
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   int32_t offchip = 1;     // off-chip test of the persistent form
@@ -871,6 +871,44 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
 }  // namespace
 
 extern "C" {
+
+ndt_status ndt_trim_candidates(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                               const int64_t* cand_idx, int64_t n_cand, float kappa, int32_t max_iter,
+                               int32_t min_obs, float* nu_out, int32_t* nkept_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "trim_candidates before load_exposures");
+  if (!(kappa > 0.0f) || max_iter < 1 || max_iter > 1000 || min_obs < 0)
+    return fail(ctx, NDT_EINVAL, "trim: kappa %g, max_iter %d, min_obs %d", kappa, max_iter, min_obs);
+  if (n_orbits < 0 || n_cand < 0 || (n_cand > 0 && (!states || !cand_idx || !nu_out)))
+    return fail(ctx, NDT_EINVAL, "bad trim arguments");
+  if (n_cand == 0) return NDT_OK;
+  const void* st_dev = nullptr;
+  ndt_status s = to_device(ctx, states, sizeof(double) * 6 * n_orbits, ctx->stage_states, &st_dev);
+  if (s != NDT_OK) return s;
+  const void* cd = nullptr;
+  if ((s = to_device(ctx, cand_idx, sizeof(int64_t) * n_cand, ctx->cand_stage, &cd)) != NDT_OK) return s;
+  float* nu = nullptr;
+  int32_t* nk = nullptr;
+  if ((s = out_buffer(ctx, nu_out, (size_t)n_cand, ctx->trim_nu, &nu)) != NDT_OK) return s;
+  if ((s = out_buffer(ctx, nkept_out, (size_t)n_cand, ctx->trim_n, &nk)) != NDT_OK) return s;
+  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp), "trim positions");
+  NDT_CK(ctx->trim_bits.ensure(4 * trim_scratch_words(n_cand, ctx->n_exp)), "trim scratch");
+  NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0,
+                                static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
+                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(),
+                                ctx->counters.as<unsigned long long>(), ctx->stream), "trim positions");
+  NDT_CK(launch_trim(ctx->stamp_pos.as<int2>(), n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp, ctx->planes.p,
+                     ctx->plane_type, kappa, max_iter, min_obs, ctx->trim_bits.as<uint32_t>(), nu, nk, nullptr,
+                     nullptr, ctx->n_sms, ctx->stream),
+         "trim kernel");
+  ctx->launches += 2;
+  if ((s = copy_out(ctx, nu_out, nu, (size_t)n_cand)) != NDT_OK) return s;
+  if ((s = copy_out(ctx, nkept_out, nk, (size_t)n_cand)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
 
 ndt_status ndt_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
                       const int64_t* cand_idx, int64_t n_cand, float* stamps_f32,

@@ -548,6 +548,11 @@ cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, c
 cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                           const void* planes, int plane_type, float* out_f32,
                           __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st);
+size_t trim_scratch_words(int64_t n_cand, int32_t n_exp);
+cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp, const void* planes,
+                        int plane_type, float kappa, int32_t max_iter, int32_t min_obs, uint32_t* keep_bits,
+                        float* nu_out, int32_t* n_out, float* psi_out, float* phi_out, int n_sms,
+                        cudaStream_t st);
 cudaError_t launch_cnn_forward_tc(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
                                   int* err, int n_sms, cudaStream_t st);
 cudaError_t launch_cnn_backward(const float* th, const __nv_bfloat16* x, const float* labels,

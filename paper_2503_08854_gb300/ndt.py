@@ -62,6 +62,7 @@ _lib.ndt_predict_positions.argtypes = [_vp, _vp, _f64, _i64, _vp]
 _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
 _lib.ndt_set_offchip_test.argtypes = [_vp, _i32]
+_lib.ndt_trim_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _i32, _vp, _vp]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
 _lib.ndt_get_stats.argtypes = [_vp, C.POINTER(Stats)]
 _lib.ndt_stamps.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, _vp, _vp]
@@ -252,6 +253,15 @@ def vet(ctx, params, states_soa, t0, n_orbits, cand_idx, scores):
                              _ptr(cand_idx), int(len(cand_idx)), _ptr(scores)))
 
 
+def trim_candidates(ctx, states_soa, t0, n_orbits, cand_idx, nu_out, nkept_out=None, kappa=3.0,
+                    max_iter=10, min_obs=1):
+    """Outlier-trimmed stacked SNR of the candidates (sigma clipping of their
+    intersections, see ndt_trim_candidates)."""
+    _check(ctx, _lib.ndt_trim_candidates(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(cand_idx),
+                                         int(len(cand_idx)), float(kappa), int(max_iter), int(min_obs),
+                                         _ptr(nu_out), _ptr(nkept_out)))
+
+
 def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
     """ndt_topk_noalloc: top-k of a device array with the library's fixed
     scratch (no device allocation); device pointers only, asynchronous on
@@ -270,4 +280,4 @@ def exported_symbols():
             "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
-            "ndt_topk_noalloc"]
+            "ndt_trim_candidates", "ndt_topk_noalloc"]
