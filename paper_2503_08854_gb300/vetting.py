@@ -81,12 +81,13 @@ def fpr_at_recall(score_pos, score_neg, recall):
     return float(np.mean(np.asarray(score_neg) >= thr)), float(thr)
 
 
-def make_set(ctx, seed, device, *, n_sky=1, noise_trials=20000, n_peaks=400, **sky_kw):
+def make_set(ctx, seed, device, *, n_sky=1, noise_trials=20000, n_peaks=400, trimmed=False, **sky_kw):
     """Stamps and labels from ``n_sky`` vetting skies.  Returns
     (stamps_bf16 (n,2,21,21) torch, labels (n,), kind (n,) numpy: 0 source,
-    1 random orbit, 2 artefact, 3 noise peak, centre SNR (n,) numpy)."""
+    1 random orbit, 2 artefact, 3 noise peak, centre SNR (n,) numpy), and with
+    ``trimmed`` also the outlier-trimmed SNR (n,) numpy."""
     import torch
-    xs, ys, kinds, snrs = [], [], [], []
+    xs, ys, kinds, snrs, trims = [], [], [], [], []
     for s in range(n_sky):
         sky = synth.vetting_sky(seed=seed * 1000 + s, **sky_kw)
         ex, n_exp = sky.ex, sky.ex.n
@@ -108,8 +109,8 @@ def make_set(ctx, seed, device, *, n_sky=1, noise_trials=20000, n_peaks=400, **s
         cand_states = np.concatenate([sky.inj_states, sky.meta["rand_states"], art])
         kind = np.concatenate([np.zeros(len(sky.inj_states)), np.ones(len(sky.meta["rand_states"])),
                                np.full(len(art), 2)]).astype(np.int64)
-        x, c0 = _stamps(ctx, cand_states, sky.t0, device)
-        xs.append(x); kinds.append(kind); snrs.append(c0)
+        x, c0, tr = _stamps(ctx, cand_states, sky.t0, device)
+        xs.append(x); kinds.append(kind); snrs.append(c0); trims.append(tr)
         # noise peaks: the strongest of many random orbits on a source-free sky
         pure = synth.noise_images_torch(ex, sky.seed + 777, device)
         torch.cuda.synchronize(device)
@@ -122,11 +123,13 @@ def make_set(ctx, seed, device, *, n_sky=1, noise_trials=20000, n_peaks=400, **s
         idx = torch.empty(n_peaks, dtype=torch.int64, device=device)
         ndt.topk_candidates(ctx, n_peaks, idx)
         peaks = trials[idx.cpu().numpy()]
-        x, c0 = _stamps(ctx, peaks, sky.t0, device)
-        xs.append(x); kinds.append(np.full(len(peaks), 3)); snrs.append(c0)
+        x, c0, tr = _stamps(ctx, peaks, sky.t0, device)
+        xs.append(x); kinds.append(np.full(len(peaks), 3)); snrs.append(c0); trims.append(tr)
     x = torch.cat(xs)
     kind = np.concatenate(kinds)
     y = torch.as_tensor((kind == 0).astype(np.float32), device=device)
+    if trimmed:
+        return x, y, kind, np.concatenate(snrs), np.concatenate(trims)
     return x, y, kind, np.concatenate(snrs)
 
 
@@ -140,13 +143,17 @@ def _predict(ctx, states, t0, n_exp, device):
 
 
 def _stamps(ctx, states, t0, device):
-    """BF16 stamps of the given orbits and their FP32 centre SNR."""
+    """BF16 stamps of the given orbits, their FP32 centre SNR and their
+    outlier-trimmed SNR (sigma clipping of the intersections, kappa 3)."""
     import torch
     n = len(states)
     st = torch.from_numpy(np.ascontiguousarray(np.asarray(states).T)).to(device)
     cand = torch.arange(n, dtype=torch.int64, device=device)
     f32 = torch.empty((n, 2, 21, 21), device=device)
     bf = torch.empty((n, 2, 21, 21), dtype=torch.bfloat16, device=device)
+    trimmed = torch.empty(n, device=device)
     torch.cuda.synchronize(device)
     ndt.stamps(ctx, st, t0, n, cand, f32, bf)
-    return bf, f32[:, 0, 10, 10].cpu().numpy().astype(np.float64)
+    ndt.trim_candidates(ctx, st, t0, n, cand, trimmed)
+    return (bf, f32[:, 0, 10, 10].cpu().numpy().astype(np.float64),
+            trimmed.cpu().numpy().astype(np.float64))

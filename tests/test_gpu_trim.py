@@ -36,7 +36,11 @@ def _sky_with_artefacts(n_art=12, seed=7):
     w, h = sky.ex.width[0], sky.ex.height[0]
     inner = (np.isfinite(xy_p[..., 0]) & (xy_p[..., 0] > 10) & (xy_p[..., 0] < w - 10) &
              (xy_p[..., 1] > 10) & (xy_p[..., 1] < h - 10))
+    # artefacts at least 30 px from the asteroid's image in their exposure
+    d_ast = np.hypot(xy_p[..., 0] - xy_inj[0, :, 0], xy_p[..., 1] - xy_inj[0, :, 1])
+    inner &= ~(d_ast < 30.0)
     order = np.argsort(-inner.sum(1), kind="stable")[:n_art]
+    assert np.all(inner[order].sum(1) >= 1)
     art_xy = np.full((n_art, sky.ex.n, 2), np.nan)
     art_j = np.zeros(n_art, np.int64)
     for a, b in enumerate(order):

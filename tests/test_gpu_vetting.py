@@ -167,3 +167,24 @@ def test_trained_vetter_beats_snr_threshold(gpu):
     fpr_snr, _ = vetting.fpr_at_recall(st[pos], st[~pos], 0.9)
     print(f"FPR at 90% recall: CNN {fpr_cnn:.3f} vs SNR threshold {fpr_snr:.3f}")
     assert fpr_cnn < 0.75 * fpr_snr
+
+
+def test_trimmed_snr_cuts_artefact_false_positives(gpu):
+    """Outlier trimming (sigma clipping of each candidate's intersections)
+    at the threshold that keeps 90 % of the injected asteroids: the
+    single-exposure artefacts that pass the plain stacked-SNR threshold
+    mostly fall below the trimmed one."""
+    _, _, kind, snr, trim = vetting.make_set(gpu.ctx, 13, gpu.dev, n_sky=2, trimmed=True)
+    pos = kind == 0
+    art = kind == 2
+    _, thr_snr = vetting.fpr_at_recall(snr[pos], snr[~pos], 0.9)
+    _, thr_trim = vetting.fpr_at_recall(trim[pos], trim[~pos], 0.9)
+    fa_snr = float(np.mean(snr[art] >= thr_snr))
+    fa_trim = float(np.mean(trim[art] >= thr_trim))
+    fpr_snr, _ = vetting.fpr_at_recall(snr[pos], snr[~pos], 0.9)
+    fpr_trim, _ = vetting.fpr_at_recall(trim[pos], trim[~pos], 0.9)
+    print(f"artefacts passing at 90% recall: SNR {fa_snr:.3f}, trimmed {fa_trim:.3f}; "
+          f"FPR {fpr_snr:.3f} vs {fpr_trim:.3f}")
+    assert fa_snr > 0.2
+    assert fa_trim < 0.5 * fa_snr
+    assert fpr_trim < fpr_snr
