@@ -72,6 +72,9 @@ struct ndt_ctx {
   // vetting
   DevBuf cand_stage, stamp_pos, stamp_f32, stamp_bf16, cnn_x, cnn_labels, cnn_out, cnn_scratch,
       cnn_params, cnn_grad, trim_bits, trim_nu, trim_n;
+  // noise estimate
+  DevBuf mad_imgs, mad_state, mad_hist, mad_stage;
+  std::vector<float> noise_sigma;   // per exposure (table order): estimated sigma, or 0 if given
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   int32_t offchip = 1;     // off-chip test of the persistent form
@@ -197,6 +200,42 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
 
 void record(ndt_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
 
+// Iterative-MAD noise estimate of device images (k_mad.cu); one round of six
+// selection passes per launch_mad_round, until every image reaches its fixed
+// point or max_rounds.  out[i] is the final state of image i.
+ndt_status mad_estimate(ndt_ctx* ctx, const std::vector<const float*>& dev_imgs,
+                        const std::vector<int64_t>& n_pix, int max_rounds, std::vector<MadState>& out) {
+  const int k = (int)dev_imgs.size();
+  out.assign(k, MadState{});
+  if (k == 0) return NDT_OK;
+  std::vector<MadImage> h(k);
+  int64_t max_n = 0;
+  for (int i = 0; i < k; ++i) {
+    h[i] = MadImage{dev_imgs[i], n_pix[i]};
+    max_n = std::max(max_n, n_pix[i]);
+  }
+  NDT_CK(ctx->mad_imgs.ensure(sizeof(MadImage) * k), "noise image table");
+  NDT_CK(ctx->mad_state.ensure(sizeof(MadState) * k), "noise state");
+  NDT_CK(ctx->mad_hist.ensure(4 * mad_hist_words(k)), "noise histogram");
+  NDT_CK(cudaMemcpyAsync(ctx->mad_imgs.p, h.data(), sizeof(MadImage) * k, cudaMemcpyHostToDevice, ctx->stream),
+         "upload");
+  NDT_CK(cudaMemsetAsync(ctx->mad_state.p, 0, sizeof(MadState) * k, ctx->stream), "memset");
+  NDT_CK(cudaMemsetAsync(ctx->mad_hist.p, 0, 4 * mad_hist_words(k), ctx->stream), "memset");
+  for (int r = 0; r < max_rounds; ++r) {
+    NDT_CK(launch_mad_round(ctx->mad_imgs.as<MadImage>(), ctx->mad_state.as<MadState>(),
+                            ctx->mad_hist.as<uint32_t>(), k, max_n, max_rounds, ctx->stream),
+           "noise kernels");
+    ctx->launches += 12;
+    NDT_CK(cudaMemcpyAsync(out.data(), ctx->mad_state.p, sizeof(MadState) * k, cudaMemcpyDeviceToHost,
+                           ctx->stream), "state D2H");
+    NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+    bool all = true;
+    for (const MadState& st : out) all = all && st.done;
+    if (all) break;
+  }
+  return NDT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -289,8 +328,8 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     if (!std::isfinite(m.mjd)) return fail(ctx, NDT_EINVAL, "exposure %d: epoch not finite", j);
     if (!(m.psf_sigma_px > 0.0f && m.psf_sigma_px <= 4.0f))
       return fail(ctx, NDT_EINVAL, "exposure %d: psf sigma %g outside (0, 4]", j, m.psf_sigma_px);
-    if (!variances && !(m.variance > 0.0f))
-      return fail(ctx, NDT_EINVAL, "exposure %d: variance must be > 0", j);
+    if (!variances && std::isnan(m.variance))
+      return fail(ctx, NDT_EINVAL, "exposure %d: variance is NaN", j);
     if (!(std::isfinite(det) && det != 0.0)) return fail(ctx, NDT_EINVAL, "exposure %d: singular CD", j);
     if (m.width < 1 || m.height < 1 || m.width > 32768 || m.height > 32768)
       return fail(ctx, NDT_EINVAL, "exposure %d: size %dx%d", j, m.width, m.height);
@@ -309,6 +348,7 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
   // plane layout (sorted order), staging of host images
   ctx->ex_host.assign(n_exp, ExpDev{});
   std::vector<PlaneJob> jobs(n_exp);
+  std::vector<double> sum_p2(n_exp);   // sum of P^2 over the PSF window
   int64_t plane_elems = 0, img_elems = 0;
   int max_tiles = 0;
   for (int s = 0; s < n_exp; ++s) {
@@ -349,6 +389,7 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
       const double vbar = variances ? 1.0 : (double)J.var_c;
       J.s_phi = (float)(sg2 * sg2 / vbar);
       J.s_psi = (float)std::sqrt(sg2 * sg2 / vbar);
+      sum_p2[s] = sg2 * sg2;
     }
     J.W = m.width;
     J.H = m.height;
@@ -389,6 +430,35 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
       }
     }
     img_off += (int64_t)meta[j].width * meta[j].height;
+  }
+  // exposures without a variance (<= 0, no variance planes): iterative MAD
+  ctx->noise_sigma.assign(n_exp, 0.0f);
+  if (!variances) {
+    std::vector<const float*> imgs;
+    std::vector<int64_t> npx;
+    std::vector<int> which;
+    for (int s = 0; s < n_exp; ++s) {
+      const ndt_exposure& m = meta[ctx->sorted_to_table[s]];
+      if (m.variance > 0.0f) continue;
+      imgs.push_back(jobs[s].image);
+      npx.push_back((int64_t)m.width * m.height);
+      which.push_back(s);
+    }
+    std::vector<MadState> est;
+    ndt_status st = mad_estimate(ctx, imgs, npx, kNoiseMaxRounds, est);
+    if (st != NDT_OK) return st;
+    for (size_t i = 0; i < which.size(); ++i) {
+      const int s = which[i];
+      const float sg = est[i].sigma;
+      if (!(sg > 0.0f) || !std::isfinite(sg))
+        return fail(ctx, NDT_EINVAL, "exposure %d: noise estimate %g is not positive",
+                    ctx->sorted_to_table[s], sg);
+      PlaneJob& J = jobs[s];
+      J.var_c = (float)((double)sg * (double)sg);
+      J.s_phi = (float)(sum_p2[s] / (double)J.var_c);
+      J.s_psi = (float)std::sqrt(sum_p2[s] / (double)J.var_c);
+      ctx->noise_sigma[ctx->sorted_to_table[s]] = sg;
+    }
   }
   NDT_CK(ctx->jobs_dev.ensure(sizeof(PlaneJob) * n_exp), "job table");
   NDT_CK(cudaMemcpyAsync(ctx->jobs_dev.p, jobs.data(), sizeof(PlaneJob) * n_exp,

@@ -78,16 +78,51 @@ struct CSum {
   __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
 };
 
+// FP64 -> FP32 by truncation on the integer pipe (exponent rebias and
+// mantissa shift of the IEEE-754 bit patterns), so that the FP64 pipe, which
+// bounds the stacking kernel, executes no conversion instruction.  Relative
+// error < 2^-23; magnitudes below 2^-126 become 0, above FP32 range infinity
+// (NaN too).
+__device__ __forceinline__ float d2f_trunc(double d) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  const unsigned sign = hi & 0x80000000u;
+  const int ex = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (ex <= 0) return __uint_as_float(sign);
+  if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned)ex << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// FP64 -> FP32 rounded to nearest (ties away from zero) on the integer pipe:
+// half an FP32 ulp is added to the FP64 bit pattern (a carry moves into the
+// exponent as it should), then the pattern is truncated.  Relative error
+// <= 2^-24, as for the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d) + (1ull << 28);
+  return d2f_trunc(__longlong_as_double((long long)b));
+}
+
+// FP32 -> FP64 exactly, on the integer pipe; subnormal FP32 values become 0,
+// infinities and NaNs stay so.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  const unsigned eh = e == 0u ? 0u : (e == 255u ? 0x7FFu : e + 896u);   // 896 = 1023 - 127
+  const unsigned hi = sign | (eh << 20) | (e == 0u ? 0u : m >> 3);
+  const unsigned lo = e == 0u ? 0u : m << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // ---------------------------------------------------------------------------
 // FP64 reciprocal by Newton-Raphson refinement of an FP32 seed (the classical
 // iteration y <- y + y (1 - x y), which squares the relative error; e.g.
-// Knuth, TAOCP vol. 2, sec. 4.3.3).  The seed is the FP32 reciprocal
-// (relative error < 2^-23); one step gives < 2^-45, two steps reach FP64
-// rounding.  Valid for |x| within the FP32 normal range.
+// Knuth, TAOCP vol. 2, sec. 4.3.3).  The seed is the FP32 reciprocal of x
+// rounded to FP32 (relative error < 2^-23, conversions on the integer pipe);
+// one step gives < 2^-46 (1.5e-14), two steps reach FP64 rounding.  Valid
+// for |x| within the FP32 normal range.
 // ---------------------------------------------------------------------------
 template <int STEPS>
 __device__ __forceinline__ double rcp_nr(double x) {
-  double y = (double)__frcp_rn((float)x);
+  double y = f2d_exact(__frcp_rn(d2f_rn(x)));
 #pragma unroll
   for (int i = 0; i < STEPS; ++i) y = fma(y, fma(-x, y, 1.0), y);
   return y;
@@ -126,18 +161,19 @@ __device__ __forceinline__ void stumpff_series(double z, double& C, double& S) {
 }
 
 __device__ __forceinline__ void stumpff(double z, double& C, double& S) {
-  const double az = fabs(z);
-  if (az < 1e-6) {
+  // tier choice by an FP32 compare (every boundary has a wide margin)
+  const float zf = d2f_trunc(z), az = fabsf(zf);
+  if (az < 1e-6f) {
     stumpff_series<3>(z, C, S);
-  } else if (az < 1e-3) {
+  } else if (az < 1e-3f) {
     stumpff_series<4>(z, C, S);
-  } else if (az < 0.05) {
+  } else if (az < 0.05f) {
     stumpff_series<6>(z, C, S);
-  } else if (az < 0.3) {
+  } else if (az < 0.3f) {
     stumpff_series<8>(z, C, S);
-  } else if (az < 1.5) {
+  } else if (az < 1.5f) {
     stumpff_series<11>(z, C, S);
-  } else if (z > 0.0) {
+  } else if (zf > 0.0f) {
     double q = sqrt(z), sn, cs;
     sincos(q, &sn, &cs);
     C = (1.0 - cs) / z;
@@ -164,6 +200,9 @@ struct OrbitConst {
   double inv_period;
   double half_period;  // steps longer than this are reduced modulo the period
   double series_dt;    // steps shorter than this use the truncated f/g series
+  // FP32 copies for branch tests (compared on the FP32 pipe): the series
+  // bound shrunk by 1e-6 so that truncated |dt| never passes it wrongly
+  float series_dt_f, half_period_f, abs_alpha_f;
   // bounds along the whole conic for the off-chip test (FP32): |d^3 r/dt^3| / 6,
   // GM / (2 q^2) >= |acceleration| / 2, and the perihelion speed v_q >= |v|
   float jerk6, half_acc, vq;
@@ -198,6 +237,9 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     const double vq2 = ph.gm * (2.0 / q - oc.alpha);
     const double K = ph.gm / (q * q * q) + vq2 / (q * q);
     oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
+    oc.series_dt_f = (float)(oc.series_dt * (1.0 - 1e-6));
+    oc.half_period_f = oc.half_period < 1e30 ? (float)oc.half_period : INFINITY;
+    oc.abs_alpha_f = (float)fabs(oc.alpha);
     // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
     // <= 4 GM v_q / q^3 anywhere on the conic (r >= q, |v| <= v_q).
     if (ph.force_free) {
@@ -291,11 +333,13 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     inv_r = 1.0 / rn;
     return 0;
   }
-  if (fabs(dt) <= oc.series_dt) {
+  const float adtf = fabsf(d2f_trunc(dt));   // |dt| truncated: never above |dt|
+  if (adtf <= oc.series_dt_f) {
     fg_series_step(ph, dt, r, v, rn, inv_r);
     return 0;
   }
-  if (fabs(dt) > oc.half_period) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
+  // (reducing a step just under half a period changes nothing: rint gives 0 or +-1)
+  if (adtf > oc.half_period_f) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
   const double alpha = oc.alpha;
   const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ph.inv_sqrt_gm;
   const double a1 = fma(-alpha, rn, 1.0);            // 1 - alpha r0
@@ -304,7 +348,8 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   const double u = sdt * inv_r;
   const double si = sig0 * inv_r;
   double chi = u * fma(u, fma(-(u * kInv6), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
-  if (fabs(alpha) * chi * chi > 0.25 || !(fabs(chi) < 1e30)) {
+  const float chif = d2f_trunc(chi);
+  if (oc.abs_alpha_f * chif * chif > 0.25f || !(fabsf(chif) < 1e30f)) {
     chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
   }
   int it;
@@ -320,17 +365,17 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     const double F = fma(sig0, chi2C, fma(a1, chi3S, fma(rn, chi, -sdt)));
     const double dF = fma(sig0, chi1mzS, fma(a1, chi2C, rn));        // = |r|
     const double d2F = fma(sig0, omzC, a1 * chi1mzS);
-    const float Ff = (float)F, dFf = (float)dF, d2Ff = (float)d2F;
+    const float Ff = d2f_trunc(F), dFf = d2f_trunc(dF), d2Ff = d2f_trunc(d2F);
     const float disc = fabsf(16.0f * dFf * dFf - 20.0f * Ff * d2Ff);
     const float delta = 5.0f * Ff / (dFf + sqrtf(disc));
     if (fabsf(delta) <= kKeplerStop) {
       // outputs at chi - delta, to first order in delta
-      const double d = (double)delta;
+      const double d = f2d_exact(delta);
       const double chi2C_c = fma(-d, chi1mzS, chi2C);
       const double f = fma(-chi2C_c, inv_r, 1.0);
       const double g = fma(-fma(-d, chi2C, chi3S), ph.inv_sqrt_gm, dt);
       const double rc = fma(-d, d2F, dF);
-      const double inv_rc = rcp_nr<1>(rc);   // 2^-45: f, g, fdot, gdot stay within 1e-13 AU
+      const double inv_rc = rcp_nr<1>(rc);   // 1.5e-14: f, g, fdot, gdot stay within 1e-13 AU
       const double fdot = -ph.sqrt_gm * fma(-d, omzC, chi1mzS) * (inv_rc * inv_r);
       const double gdot = fma(-chi2C_c, inv_rc, 1.0);
       double rr[3];
@@ -341,7 +386,7 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
       inv_r = inv_rc;
       return it;
     }
-    chi -= (double)delta;
+    chi -= f2d_exact(delta);
   }
   return -1;
 }
@@ -364,12 +409,15 @@ __device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], 
     rho[0] = d[0]; rho[1] = d[1]; rho[2] = d[2];
     return;
   }
+  // |d|^2, d.v and the products t v, h r stay FP64: at 0.2 arcsec pixels the
+  // nearest-pixel decision needs rho to ~1e-12 AU, which an FP32 correction
+  // (~1e-4 AU to 2^-24) does not give.  The conversions run on the integer pipe.
   const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
   const double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
-  const float tau = fmaf(-(float)dv, ph.inv_c2, __fsqrt_rn((float)dd) * ph.inv_c);
-  const float irf = (float)inv_r;
+  const float tau = fmaf(-d2f_rn(dv), ph.inv_c2, __fsqrt_rn(d2f_rn(dd)) * ph.inv_c);
+  const float irf = d2f_rn(inv_r);
   const float hf = ph.force_free ? 0.0f : -0.5f * ph.gm_f * irf * irf * irf * tau * tau;
-  const double t = (double)tau, h = (double)hf;
+  const double t = f2d_exact(tau), h = f2d_exact(hf);
   for (int i = 0; i < 3; ++i) rho[i] = fma(h, r[i], fma(-t, v[i], d[i]));
 }
 
@@ -377,10 +425,12 @@ __device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], 
 // Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
 // Returns false when cos c <= 0.
 // The reciprocal of rho . p0 needs ~1e-12 relative accuracy (x within 1e-8 px
-// at 4096 px from CRPIX): one Newton step from the FP32 seed gives < 2^-45.
+// at 4096 px from CRPIX): one Newton step from the FP32 seed gives < 1.5e-14.
+// The cos c > 0 test is an FP32 compare (the threshold only keeps the
+// reciprocal in range).
 __device__ __forceinline__ bool project(const ExpDev& e, const double rho[3], double& x, double& y) {
   const double den = rho[0] * e.p0[0] + rho[1] * e.p0[1] + rho[2] * e.p0[2];
-  if (!(den > 1e-30)) return false;
+  if (!(d2f_trunc(den) > 1e-30f)) return false;
   const double inv = rcp_nr<1>(den);
   x = fma(rho[0] * e.ax[0] + rho[1] * e.ax[1] + rho[2] * e.ax[2], inv, e.crpix[0]);
   y = fma(rho[0] * e.ay[0] + rho[1] * e.ay[1] + rho[2] * e.ay[2], inv, e.crpix[1]);
@@ -394,19 +444,6 @@ __device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double x, double 
   ix = __double2int_rd(x + 0.5);
   iy = __double2int_rd(y + 0.5);
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
-}
-
-// FP64 -> FP32 by truncation on the integer pipe (exponent rebias and
-// mantissa shift of the IEEE-754 bit patterns), so the FP64 pipe that bounds
-// the stacking kernel does no conversions for the off-chip test.  Relative
-// error < 2^-23; magnitudes below 2^-126 become 0, above FP32 range infinity.
-__device__ __forceinline__ float d2f_trunc(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned sign = hi & 0x80000000u;
-  const int ex = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  if (ex <= 0) return __uint_as_float(sign);
-  if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
-  return __uint_as_float(sign | ((unsigned)ex << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
 }
 
 // Off-chip test of the persistent form (FP32, no FP64 instruction).  From the
@@ -548,6 +585,25 @@ cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, c
 cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                           const void* planes, int plane_type, float* out_f32,
                           __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st);
+// Iterative-MAD noise estimate (k_mad.cu): one image and its round state.
+struct MadImage {
+  const float* x;
+  int64_t n;
+};
+struct MadState {
+  int32_t done, round, rounds, pad_;
+  long long n_kept;
+  unsigned long long krem;   // rank still wanted inside the chosen digits
+  uint32_t prefix;           // digits chosen so far
+  float m_prev, thr_prev;    // S_i = { |x - m_prev| <= thr_prev } (round > 0)
+  float m_cur;               // median of this round
+  float m_last, sigma;       // the last completed round's (median, sigma)
+};
+constexpr int kNoiseMaxRounds = 10;
+cudaError_t launch_mad_round(const MadImage* imgs, MadState* st, uint32_t* hist, int n_images,
+                             int64_t max_pixels, int max_rounds, cudaStream_t stream);
+size_t mad_hist_words(int n_images);
+
 size_t trim_scratch_words(int64_t n_cand, int32_t n_exp);
 cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp, const void* planes,
                         int plane_type, float kappa, int32_t max_iter, int32_t min_obs, uint32_t* keep_bits,
