@@ -45,8 +45,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 FP64_PER_SAMPLE = {"mba": (144.1, 98.6), "batched": (154.1, 102.8)}
 # DRAM bytes (read + write) of one full-size persistent stack launch (BF16
 # planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
-# in a one-pass capture; None until measured on the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
+# in a one-pass capture: MBA 1.86 GB + 71.8 MB, batched 3.54 GB + 274.5 MB.
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.932e9, "batched": 3.814e9}
 
 
 def parse():
@@ -71,6 +71,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--tiles", default=None, help="fixed OT,ET for the persistent form (no autotune)")
     p.add_argument("--no-vet", action="store_true", help="skip the CNN vetting stage")
+    p.add_argument("--no-noise", action="store_true", help="skip the iterative-MAD noise timing")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
     p.add_argument("--vet-batch", type=int, default=1 << 20,
                    help="candidates of the separately timed vetting pass (0: skip)")
@@ -353,6 +354,30 @@ def vet_batch_rate(args, ctx, stream, sky, states, vet_params, device):
             "exposures": int(sky.ex.n)}
 
 
+def noise_rate(device, stream, imgs):
+    """Iterative-MAD noise estimate of every image (ndt_noise_mad), timed
+    with CUDA events; its roofline is the HBM read rate (each selection pass
+    streams the image once: 6 passes per round)."""
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    ctx = ndt.create(device.index, stream)
+    try:
+        views = [imgs[j] for j in range(imgs.shape[0])]
+        ndt.noise_mad(ctx, views)                                   # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        med, sig, rnd = ndt.noise_mad(ctx, views)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        ndt.destroy(ctx)
+    read = float(np.sum(6 * rnd.astype(np.float64) * 4 * views[0].numel()))
+    return {"images": len(views), "ms": ms, "rounds_max": int(rnd.max()), "rounds_mean": float(rnd.mean()),
+            "read_bytes": read, "read_gbps": read / (ms / 1e3) / 1e9}
+
+
 def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
     """Same steps through the public API with pinned HOST inputs and outputs:
     the H2D copies of images and orbit states and the D2H read of the top-k
@@ -574,6 +599,8 @@ def main():
         line["e2e"] = {"value": samples * world / max_over_ranks(e2e["s_per_step"]), "unit": UNIT,
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                        "recall_in_topk": e2e["recall_in_topk"]}
+    if rank == 0 and args.workload == "mba" and not args.no_noise:
+        line["noise_estimate"] = noise_rate(device, stream, imgs)
     if rank == 0 and not args.no_cpu:
         host = imgs.cpu().numpy()
         rate, cores, desc = cpu_oracle_rate(sky, host, args.cpu_seconds)

@@ -77,8 +77,9 @@ typedef struct {
   double cd[4];        /* CD matrix row-major: [CD1_1 CD1_2 CD2_1 CD2_2],
                           degrees per pixel                                */
   float psf_sigma_px;  /* Gaussian PSF sigma, pixels, in (0, 4]            */
-  float variance;      /* constant per-pixel noise variance (> 0), used
-                          when no variance plane is given                  */
+  float variance;      /* constant per-pixel noise variance, used when no
+                          variance plane is given; <= 0: estimate it by the
+                          iterative MAD of the image                       */
   int32_t width;       /* pixels, 1 .. 32768                               */
   int32_t height;      /* pixels, 1 .. 32768                               */
 } ndt_exposure;
@@ -130,10 +131,12 @@ ndt_status ndt_set_constants(ndt_ctx *ctx, double gm, double c_light, double obl
  * normalised to unit sum over its (2R+1)^2 window; terms outside the image
  * are dropped.  `images[j]` is a row-major FP32 height x width image;
  * `variances` is NULL (constant variance from the table) or n_exp per-pixel
- * FP32 variance planes of the same shape.  `plane_dtype` is an
- * ndt_plane_dtype.  Replaces any previous exposure set.  Returns NDT_EINVAL
- * for n_exp < 1, a null image, sigma outside (0, 4], variance <= 0, a
- * singular CD matrix or a non-finite epoch.
+ * FP32 variance planes of the same shape.  With `variances` NULL, an
+ * exposure whose table variance is <= 0 gets the iterative-MAD estimate of
+ * ndt_noise_mad (variance = sigma^2).  `plane_dtype` is an ndt_plane_dtype.
+ * Replaces any previous exposure set.  Returns NDT_EINVAL for n_exp < 1, a
+ * null image, sigma outside (0, 4], a NaN variance, a noise estimate that
+ * is not positive, a singular CD matrix or a non-finite epoch.
  */
 ndt_status ndt_load_exposures(ndt_ctx *ctx, const ndt_exposure *meta, int32_t n_exp,
                               const float *const *images, const float *const *variances,
@@ -263,6 +266,25 @@ ndt_status ndt_cnn_loss_grad(ndt_ctx *ctx, const float *params, const uint16_t *
 ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, float *m, float *v,
                              int64_t n_params, int32_t step, float lr, float beta1, float beta2,
                              float eps);
+
+/*
+ * noise_mad: per-image noise by the iterative median absolute deviation
+ * (paper sec. 3: pixel noise variance from an iterative version of the MAD
+ * on each image's pixels).  For image i (n_pixels[i] FP32 values at
+ * images[i], host or device memory), with S_0 = every pixel:
+ *   m = lower median of S (the element of rank floor((n-1)/2)),
+ *   sigma = fl32(1.4826 * lower median of fl32|x - m| over S),
+ *   S' = { x : fl32|x - m| <= fl32(3 sigma) } over every pixel,
+ * repeated until (m, sigma) repeats or max_rounds (1..100) rounds; outputs
+ * median_out[i], sigma_out[i] and rounds_out[i] (any may be NULL; host or
+ * device, caller-owned).  The result is exact: FP32 operations as written
+ * and exact order statistics.  An image with no pixels gives NaN.
+ * load_exposures uses the same estimate (variance = sigma^2) for exposures
+ * whose variance is <= 0 when no variance planes are given.  Synchronous.
+ */
+ndt_status ndt_noise_mad(ndt_ctx *ctx, const float *const *images, const int64_t *n_pixels,
+                         int32_t n_images, int32_t max_rounds, float *median_out, float *sigma_out,
+                         int32_t *rounds_out);
 
 /*
  * trim_candidates: outlier trimming of candidates' intersections (paper

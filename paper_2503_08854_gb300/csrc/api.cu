@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -941,6 +942,61 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
 }  // namespace
 
 extern "C" {
+
+ndt_status ndt_noise_mad(ndt_ctx* ctx, const float* const* images, const int64_t* n_pixels,
+                         int32_t n_images, int32_t max_rounds, float* median_out, float* sigma_out,
+                         int32_t* rounds_out) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (n_images < 0 || (n_images > 0 && (!images || !n_pixels)) || max_rounds < 1 || max_rounds > 100)
+    return fail(ctx, NDT_EINVAL, "noise_mad: bad arguments");
+  if (n_images == 0) return NDT_OK;
+  std::vector<const float*> dev(n_images);
+  std::vector<int64_t> npx(n_pixels, n_pixels + n_images);
+  int64_t host_total = 0;
+  for (int i = 0; i < n_images; ++i) {
+    if (npx[i] < 0 || (npx[i] > 0 && !images[i])) return fail(ctx, NDT_EINVAL, "noise_mad: image %d", i);
+    if (npx[i] > 0 && !is_device_ptr(images[i])) host_total += npx[i];
+  }
+  if (host_total) NDT_CK(ctx->mad_stage.ensure(sizeof(float) * host_total), "noise staging");
+  int64_t off = 0;
+  for (int i = 0; i < n_images; ++i) {
+    if (npx[i] == 0 || is_device_ptr(images[i])) {
+      dev[i] = images[i];
+      continue;
+    }
+    float* dst = ctx->mad_stage.as<float>() + off;
+    NDT_CK(cudaMemcpyAsync(dst, images[i], sizeof(float) * npx[i], cudaMemcpyHostToDevice, ctx->stream), "H2D");
+    dev[i] = dst;
+    off += npx[i];
+  }
+  std::vector<MadState> st;
+  ndt_status s = mad_estimate(ctx, dev, npx, max_rounds, st);
+  if (s != NDT_OK) return s;
+  std::vector<float> med(n_images), sig(n_images);
+  std::vector<int32_t> rnd(n_images);
+  for (int i = 0; i < n_images; ++i) {
+    med[i] = st[i].m_last;
+    sig[i] = st[i].sigma;
+    rnd[i] = st[i].rounds;
+    if (npx[i] == 0) med[i] = sig[i] = std::numeric_limits<float>::quiet_NaN();
+  }
+  auto put = [&](auto* user, const auto& v) -> ndt_status {
+    if (!user) return NDT_OK;
+    const size_t bytes = sizeof(v[0]) * v.size();
+    if (is_device_ptr(user)) {
+      NDT_CK(cudaMemcpyAsync(user, v.data(), bytes, cudaMemcpyHostToDevice, ctx->stream), "output H2D");
+    } else {
+      std::memcpy(user, v.data(), bytes);
+    }
+    return NDT_OK;
+  };
+  if ((s = put(median_out, med)) != NDT_OK) return s;
+  if ((s = put(sigma_out, sig)) != NDT_OK) return s;
+  if ((s = put(rounds_out, rnd)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
 
 ndt_status ndt_trim_candidates(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
                                const int64_t* cand_idx, int64_t n_cand, float kappa, int32_t max_iter,

@@ -63,6 +63,7 @@ _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
 _lib.ndt_set_offchip_test.argtypes = [_vp, _i32]
 _lib.ndt_trim_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _i32, _vp, _vp]
+_lib.ndt_noise_mad.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_i64), _i32, _i32, _vp, _vp, _vp]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
 _lib.ndt_get_stats.argtypes = [_vp, C.POINTER(Stats)]
 _lib.ndt_stamps.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, _vp, _vp]
@@ -253,6 +254,20 @@ def vet(ctx, params, states_soa, t0, n_orbits, cand_idx, scores):
                              _ptr(cand_idx), int(len(cand_idx)), _ptr(scores)))
 
 
+def noise_mad(ctx, images, max_rounds=10):
+    """Iterative-MAD noise estimate of each image (ndt_noise_mad).  ``images``:
+    a sequence of FP32 numpy arrays or torch tensors (host or device).
+    Returns numpy arrays (median, sigma, rounds)."""
+    n = len(images)
+    ptrs = (_vp * max(n, 1))(*[_ptr(x) for x in images])
+    npx = (_i64 * max(n, 1))(*[int(x.numel() if hasattr(x, "numel") else x.size) for x in images])
+    med = np.zeros(n, np.float32)
+    sig = np.zeros(n, np.float32)
+    rnd = np.zeros(n, np.int32)
+    _check(ctx, _lib.ndt_noise_mad(ctx, ptrs, npx, n, int(max_rounds), _ptr(med), _ptr(sig), _ptr(rnd)))
+    return med, sig, rnd
+
+
 def trim_candidates(ctx, states_soa, t0, n_orbits, cand_idx, nu_out, nkept_out=None, kappa=3.0,
                     max_iter=10, min_obs=1):
     """Outlier-trimmed stacked SNR of the candidates (sigma clipping of their
@@ -280,4 +295,4 @@ def exported_symbols():
             "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
-            "ndt_trim_candidates", "ndt_topk_noalloc"]
+            "ndt_trim_candidates", "ndt_noise_mad", "ndt_topk_noalloc"]
