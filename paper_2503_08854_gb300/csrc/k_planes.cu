@@ -21,49 +21,72 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <int MODE>
+// Tile geometry for a compile-time window radius RM >= the jobs' R: the
+// weights are zero-padded to 2 RM + 1 taps, which adds exact zeros in the same
+// accumulation order (the planes are bit-identical to an R-tap loop) and lets
+// every tap loop unroll.
+template <int RM>
+struct PlaneGeom {
+  static constexpr int E = kTile + 2 * RM;   // input tile edge
+  static constexpr int ES = E + 1;           // odd row stride: conflict-free horizontal pass
+  static constexpr int HS = kTile + 1;       // row stride of the horizontal results (odd)
+  static constexpr int NT = 2 * RM + 1;      // taps
+  static constexpr int HW = 8;               // horizontal outputs per thread (sliding window)
+  static constexpr int VH = 4;               // vertical outputs per thread
+  static constexpr int SMEM_FLOATS = 144 + 2 * (E * ES + E * HS);
+};
+
+template <int MODE, int RM>
 __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict__ jobs,
                                                      void* __restrict__ out,
                                                      unsigned int* __restrict__ absmax2) {
+  using G = PlaneGeom<RM>;
+  constexpr int E = G::E, ES = G::ES, HS = G::HS, NT = G::NT, HW = G::HW, VH = G::VH;
+  static_assert(kThreads == kTile * (kTile / VH), "vertical pass: one thread per (column, strip)");
   const PlaneJob& J = jobs[blockIdx.y];
   const int tile = blockIdx.x;
   const int tiles_x = J.tiles_x, W = J.W, H = J.H;
   if (tile >= tiles_x * J.tiles_y) return;
   const int tx = tile % tiles_x, ty = tile / tiles_x;
   const int R = J.R;
-  const int E = kTile + 2 * R;                 // input tile edge
   extern __shared__ float sm[];
-  float* gw = sm;                              // 2R+1 (<= 33)
+  float* gw = sm;                              // NT (<= 33) zero-padded weights
   float* gw2 = sm + 40;
   float* ex = sm + 80;                         // 32: sum of g^2 inside the image along x
   float* ey = sm + 112;                        // 32: same along y
-  float* in = sm + 144;                        // E x E  : I / V
-  float* hor = in + E * E;                     // E x 32 : horizontal pass of psi
-  float* inw = hor + E * kTile;                // E x E  : 1 / V   (variance plane only)
-  float* horw = inw + E * E;                   // E x 32
+  float* in = sm + 144;                        // E rows of stride ES : I / V
+  float* hor = in + E * ES;                    // E rows of stride HS : horizontal pass of psi
+  float* inw = hor + E * HS;                   // E rows of stride ES : 1 / V (variance plane only)
+  float* horw = inw + E * ES;                  // E rows of stride HS
   const bool vplane = J.var != nullptr;
-  const int n2 = 2 * R + 1;
-  if (threadIdx.x < n2) {
-    gw[threadIdx.x] = J.g[threadIdx.x];
-    gw2[threadIdx.x] = J.g2[threadIdx.x];
+  if (threadIdx.x < NT) {
+    const int k = (int)threadIdx.x - RM;
+    const bool inside = k >= -R && k <= R;
+    gw[threadIdx.x] = inside ? J.g[k + R] : 0.0f;
+    gw2[threadIdx.x] = inside ? J.g2[k + R] : 0.0f;
   }
-  const int x0 = tx * kTile - R, y0 = ty * kTile - R;
+  const int x0 = tx * kTile - RM, y0 = ty * kTile - RM;
   const float inv_vc = 1.0f / J.var_c;
-  for (int i = threadIdx.x; i < E * E; i += kThreads) {
-    const int yy = y0 + i / E, xx = x0 + i % E;
-    float a = 0.0f, w = 0.0f;
-    if (xx >= 0 && xx < W && yy >= 0 && yy < H) {
-      const int64_t p = (int64_t)yy * W + xx;
-      const float I = __ldg(J.image + p);
-      if (vplane) {
-        w = 1.0f / __ldg(J.var + p);
-        a = I * w;
-      } else {
-        a = I * inv_vc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < E; r += kThreads / 32) {          // rows by warps, columns by lanes
+    const int yy = y0 + r;
+    const bool row_in = yy >= 0 && yy < H;
+    for (int c = lane; c < E; c += 32) {
+      const int xx = x0 + c;
+      float a = 0.0f, w = 0.0f;
+      if (row_in && xx >= 0 && xx < W) {
+        const int64_t p = (int64_t)yy * W + xx;
+        const float I = __ldg(J.image + p);
+        if (vplane) {
+          w = 1.0f / __ldg(J.var + p);
+          a = I * w;
+        } else {
+          a = I * inv_vc;
+        }
       }
+      in[r * ES + c] = a;
+      if (vplane) inw[r * ES + c] = w;
     }
-    in[i] = a;
-    if (vplane) inw[i] = w;
   }
   __syncthreads();
   if (!vplane && threadIdx.x < 2 * kTile) {
@@ -73,23 +96,48 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     const int c = (along_x ? tx : ty) * kTile + (threadIdx.x % kTile);
     const int lim = along_x ? W : H;
     float s = 0.0f;
-    for (int k = 0; k < n2; ++k) {
-      const int q = c + k - R;
+    for (int k = 0; k < NT; ++k) {
+      const int q = c + k - RM;
       if (q >= 0 && q < lim) s += gw2[k];
     }
     (along_x ? ex : ey)[threadIdx.x % kTile] = s;
   }
-  for (int i = threadIdx.x; i < E * kTile; i += kThreads) {
-    const int r = i / kTile, c = i % kTile;
-    const float* row = in + r * E + c;
-    float acc = 0.0f;
-    for (int k = 0; k < n2; ++k) acc = fmaf(gw[k], row[k], acc);
-    hor[i] = acc;
+  // horizontal pass: a thread slides a register window along HW outputs
+  for (int item = threadIdx.x; item < E * (kTile / HW); item += kThreads) {
+    const int r = item / (kTile / HW), c0 = (item % (kTile / HW)) * HW;
+    {
+      float w[HW + 2 * RM];
+      const float* row = in + r * ES + c0;
+#pragma unroll
+      for (int t = 0; t < HW + 2 * RM; ++t) w[t] = row[t];
+      float acc[HW];
+#pragma unroll
+      for (int j = 0; j < HW; ++j) acc[j] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NT; ++k) {
+        const float g = gw[k];
+#pragma unroll
+        for (int j = 0; j < HW; ++j) acc[j] = fmaf(g, w[j + k], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < HW; ++j) hor[r * HS + c0 + j] = acc[j];
+    }
     if (vplane) {
-      const float* roww = inw + r * E + c;
-      float accw = 0.0f;
-      for (int k = 0; k < n2; ++k) accw = fmaf(gw2[k], roww[k], accw);
-      horw[i] = accw;
+      float w[HW + 2 * RM];
+      const float* row = inw + r * ES + c0;
+#pragma unroll
+      for (int t = 0; t < HW + 2 * RM; ++t) w[t] = row[t];
+      float acc[HW];
+#pragma unroll
+      for (int j = 0; j < HW; ++j) acc[j] = 0.0f;
+#pragma unroll
+      for (int k = 0; k < NT; ++k) {
+        const float g = gw2[k];
+#pragma unroll
+        for (int j = 0; j < HW; ++j) acc[j] = fmaf(g, w[j + k], acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < HW; ++j) horw[r * HS + c0 + j] = acc[j];
     }
   }
   __syncthreads();
@@ -103,27 +151,52 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     s0 = a0 > 0.0f ? a0 / 16384.0f : 1.0f;
     s1 = a1 > 0.0f ? a1 / 16384.0f : 1.0f;
   }
-  const int64_t base = J.plane_off + ((int64_t)tile << (2 * kTileShift));
-  for (int i = threadIdx.x; i < kTile * kTile; i += kThreads) {
-    const int y = i >> kTileShift, x = i & (kTile - 1);
-    float psi = 0.0f, phi = 0.0f;
-    for (int k = 0; k < n2; ++k) psi = fmaf(gw[k], hor[(y + k) * kTile + x], psi);
-    if (vplane) {
-      for (int k = 0; k < n2; ++k) phi = fmaf(gw2[k], horw[(y + k) * kTile + x], phi);
-    } else {
-      phi = ex[x] * ey[y] * inv_vc;
+  // vertical pass: thread (column x, strip of VH rows)
+  const int x = threadIdx.x & (kTile - 1), ys = (threadIdx.x / kTile) * VH;
+  float psi[VH], phi[VH];
+  {
+    float v[VH + 2 * RM];
+#pragma unroll
+    for (int t = 0; t < VH + 2 * RM; ++t) v[t] = hor[(ys + t) * HS + x];
+#pragma unroll
+    for (int j = 0; j < VH; ++j) psi[j] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const float g = gw[k];
+#pragma unroll
+      for (int j = 0; j < VH; ++j) psi[j] = fmaf(g, v[j + k], psi[j]);
     }
+  }
+  if (vplane) {
+    float v[VH + 2 * RM];
+#pragma unroll
+    for (int t = 0; t < VH + 2 * RM; ++t) v[t] = horw[(ys + t) * HS + x];
+#pragma unroll
+    for (int j = 0; j < VH; ++j) phi[j] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NT; ++k) {
+      const float g = gw2[k];
+#pragma unroll
+      for (int j = 0; j < VH; ++j) phi[j] = fmaf(g, v[j + k], phi[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < VH; ++j) phi[j] = ex[x] * ey[ys + j] * inv_vc;
+  }
+  const int64_t base = J.plane_off + ((int64_t)tile << (2 * kTileShift));
+#pragma unroll
+  for (int j = 0; j < VH; ++j) {
+    const int y = ys + j, i = (y << kTileShift) + x;
     if (MODE == kPlaneStoreF32) {
-      reinterpret_cast<float2*>(out)[base + i] = make_float2(psi, phi);
+      reinterpret_cast<float2*>(out)[base + i] = make_float2(psi[j], phi[j]);
     } else if (MODE == kPlaneAbsMax) {
       if (tx * kTile + x < W && ty * kTile + y < H) {
-        m0 = fmaxf(m0, fabsf(psi));
-        m1 = fmaxf(m1, fabsf(phi));
+        m0 = fmaxf(m0, fabsf(psi[j]));
+        m1 = fmaxf(m1, fabsf(phi[j]));
       }
     } else {
-      // round-to-nearest-even of value / scale; the scale maps the plane's
-      // largest magnitude to 2^14
-      const float q0 = __fdiv_rn(psi, s0), q1 = __fdiv_rn(phi, s1);
+      // round-to-nearest-even of value / scale
+      const float q0 = __fdiv_rn(psi[j], s0), q1 = __fdiv_rn(phi[j], s1);
       if (MODE == kPlaneStoreBF16)
         reinterpret_cast<__nv_bfloat162*>(out)[base + i] =
             __halves2bfloat162(__float2bfloat16_rn(q0), __float2bfloat16_rn(q1));
@@ -168,24 +241,26 @@ __global__ void __launch_bounds__(kThreads) k_plane_decode(const void* __restric
   }
 }
 
-size_t planes_smem_bytes(int R, bool vplane) {
-  const int E = kTile + 2 * R;
-  size_t f = 144 + (size_t)E * E + (size_t)E * kTile;
-  if (vplane) f += (size_t)E * E + (size_t)E * kTile;
-  return f * sizeof(float);
+template <int MODE, int RM>
+cudaError_t launch_rm(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, bool any_var, void* out,
+                      unsigned int* absmax2, cudaStream_t st) {
+  using G = PlaneGeom<RM>;
+  // the variance-plane half of the buffers is only needed with variance planes
+  const size_t smem = sizeof(float) * (any_var ? G::SMEM_FLOATS : 144 + G::E * G::ES + G::E * G::HS);
+  cudaError_t e = cudaFuncSetAttribute(k_planes<MODE, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(float) * G::SMEM_FLOATS));
+  if (e != cudaSuccess) return e;
+  dim3 grid(max_tiles, n_jobs);
+  k_planes<MODE, RM><<<grid, kThreads, smem, st>>>(jobs_dev, out, absmax2);
+  return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t launch_mode(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
                         void* out, unsigned int* absmax2, cudaStream_t st) {
-  // sized for the largest window radius among the jobs
-  const size_t smem = planes_smem_bytes(max_R, any_var);
-  cudaError_t e = cudaFuncSetAttribute(k_planes<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)planes_smem_bytes(kMaxPsfRadius, true));
-  if (e != cudaSuccess) return e;
-  dim3 grid(max_tiles, n_jobs);
-  k_planes<MODE><<<grid, kThreads, smem, st>>>(jobs_dev, out, absmax2);
-  return cudaGetLastError();
+  // the window radius of the launch covers the largest one among the jobs
+  if (max_R <= 8) return launch_rm<MODE, 8>(jobs_dev, n_jobs, max_tiles, any_var, out, absmax2, st);
+  return launch_rm<MODE, kMaxPsfRadius>(jobs_dev, n_jobs, max_tiles, any_var, out, absmax2, st);
 }
 
 }  // namespace

@@ -83,64 +83,57 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
   }
 }
 
-// Exposures are taken kStampUnroll at a time: every thread issues the
-// gathers of all of them before accumulating (in exposure order), so several
-// independent loads are in flight per thread instead of one.
+// One thread per stamp pixel (448 threads, 441 active); exposures are taken
+// kStampUnroll at a time: every thread issues the gathers of all of them
+// before accumulating (in exposure order), so several independent loads are
+// in flight per thread.
 constexpr int kStampUnroll = 4;
+constexpr int kStampThreads = 448;
 
 template <int PT>
-__global__ void __launch_bounds__(kVetThreads) k_stamps(const int2* __restrict__ pos, int64_t n_cand,
-                                                         const ExpDev* __restrict__ ex, int32_t n_exp,
-                                                         const void* __restrict__ planes,
-                                                         float* __restrict__ out_f32,
-                                                         __nv_bfloat16* __restrict__ out_bf16) {
+__global__ void __launch_bounds__(kStampThreads) k_stamps(const int2* __restrict__ pos, int64_t n_cand,
+                                                          const ExpDev* __restrict__ ex, int32_t n_exp,
+                                                          const void* __restrict__ planes,
+                                                          float* __restrict__ out_f32,
+                                                          __nv_bfloat16* __restrict__ out_bf16) {
+  const int p = threadIdx.x;
+  const int dx = p % S - S / 2, dy = p / S - S / 2;
   for (int64_t c = blockIdx.x; c < n_cand; c += gridDim.x) {
-    CSum sp[2], sf[2], sq[2];
-    int cnt[2] = {0, 0};
-    for (int k = 0; k < 2; ++k) sp[k] = sf[k] = sq[k] = CSum{0.0f, 0.0f};
-    const int p0 = threadIdx.x, p1 = threadIdx.x + kVetThreads;
+    CSum sp{0.0f, 0.0f}, sf{0.0f, 0.0f}, sq{0.0f, 0.0f};
+    int cnt = 0;
     const int2* cpos = pos + c * n_exp;
     for (int j0 = 0; j0 < n_exp; j0 += kStampUnroll) {
-      float2 v[kStampUnroll][2];
-      bool ok[kStampUnroll][2];
+      float2 v[kStampUnroll];
+      bool ok[kStampUnroll];
 #pragma unroll
       for (int u = 0; u < kStampUnroll; ++u) {
         const int j = j0 + u;
-        const int2 ctr = j < n_exp ? cpos[j] : make_int2(INT_MIN, INT_MIN);
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int p = k ? p1 : p0;
-          ok[u][k] = false;
-          v[u][k] = make_float2(0.0f, 0.0f);
-          if (ctr.x == INT_MIN || p >= NPIX) continue;
-          const ExpDev& e = ex[j];
-          const int px = ctr.x + p % S - S / 2, py = ctr.y + p / S - S / 2;
-          if ((unsigned)px >= (unsigned)e.W || (unsigned)py >= (unsigned)e.H) continue;
-          v[u][k] = gather_plane<PT>(planes, e, px, py);
-          ok[u][k] = true;
-        }
+        ok[u] = false;
+        v[u] = make_float2(0.0f, 0.0f);
+        if (j >= n_exp || p >= NPIX) continue;
+        const int2 ctr = cpos[j];
+        if (ctr.x == INT_MIN) continue;
+        const ExpDev& e = ex[j];
+        const int px = ctr.x + dx, py = ctr.y + dy;
+        if ((unsigned)px >= (unsigned)e.W || (unsigned)py >= (unsigned)e.H) continue;
+        v[u] = gather_plane<PT>(planes, e, px, py);
+        ok[u] = true;
       }
 #pragma unroll
       for (int u = 0; u < kStampUnroll; ++u) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (!ok[u][k] || !(v[u][k].y > 0.0f)) continue;
-          sp[k].add(v[u][k].x);
-          sf[k].add(v[u][k].y);
-          sq[k].add(__fdividef(v[u][k].x * v[u][k].x, v[u][k].y));   // ~2 ulp
-          cnt[k] += 1;
-        }
+        if (!ok[u] || !(v[u].y > 0.0f)) continue;
+        sp.add(v[u].x);
+        sf.add(v[u].y);
+        sq.add(__fdividef(v[u].x * v[u].x, v[u].y));   // ~2 ulp
+        cnt += 1;
       }
     }
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int p = k ? p1 : p0;
-      if (p >= NPIX) continue;
-      const float P = sp[k].value(), F = sf[k].value(), Q = sq[k].value();
+    if (p < NPIX) {
+      const float P = sp.value(), F = sf.value(), Q = sq.value();
       const float ch0 = F > 0.0f ? __fdiv_rn(P, __fsqrt_rn(F)) : 0.0f;
       float ch1 = 0.0f;
-      if (cnt[k] >= 2) {
-        const float m = (float)(cnt[k] - 1);
+      if (cnt >= 2) {
+        const float m = (float)(cnt - 1);
         ch1 = __fdiv_rn(Q - __fdiv_rn(P * P, F) - m, __fsqrt_rn(2.0f * m));
       }
       const int64_t base = c * 2 * NPIX;
@@ -458,11 +451,11 @@ cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int
   if (n_cand == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>(n_cand, (int64_t)n_sms * 16);
   if (plane_type == kF32)
-    k_stamps<kF32><<<blocks, kVetThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kF32><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   else if (plane_type == kBF16)
-    k_stamps<kBF16><<<blocks, kVetThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kBF16><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   else
-    k_stamps<kF16><<<blocks, kVetThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kF16><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   return cudaGetLastError();
 }
 
