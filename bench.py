@@ -478,7 +478,7 @@ def reference_arm(args):
                             fam_size=args.fam_size, seed=2, scale_arcsec=10.5 * 4096 / args.size)
     imgs = synth.noise_images(sky.ex, sky.seed)   # numpy noise: the rate does not depend on values
     threads = os.cpu_count() or 1
-    per_step = 2000
+    per_step = min(2000, len(sky.states))
     rng = np.random.default_rng(1)
 
     def step():

@@ -198,6 +198,16 @@ ndt_status ndt_get_planes(ndt_ctx *ctx, int32_t j, float *psi_out, float *phi_ou
 ndt_status ndt_set_launch(ndt_ctx *ctx, int32_t mode, int32_t orbit_tile, int32_t exp_tile,
                           int32_t use_graph);
 
+/* Filter broadening for coarse searches (paper sec. 5.2.4: smoothing the
+   images with a Gaussian wider than the PSF lets orbits be sampled more
+   sparsely while still gaining signal from objects on adjacent orbits).
+   From the next load_exposures on, the matched filter of exposure j uses the
+   Gaussian of sigma_j' = sqrt(sigma_j^2 + sigma_px^2), the PSF smoothed by a
+   Gaussian of sigma_px; 0 (the default) restores the plain filter.
+   sigma_px must be finite and >= 0 (else NDT_EINVAL); load_exposures returns
+   NDT_EINVAL when a broadened sigma exceeds 4 px. */
+ndt_status ndt_set_filter_broadening(ndt_ctx *ctx, float sigma_px);
+
 /* Off-chip test of the persistent form (on by default; the plain form never
    uses it).  Before the FP64 step of a sample, an FP32 second-order
    prediction of its pixel with a rigorous error bound (Taylor remainder from

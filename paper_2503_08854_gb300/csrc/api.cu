@@ -79,6 +79,7 @@ struct ndt_ctx {
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   int32_t offchip = 1;     // off-chip test of the persistent form
+  float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned char> graph_key;
@@ -197,6 +198,13 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   }
   const double th = std::atan(rmax) + 0.01;
   e.cos_far = th < 0.5 * kPi ? (float)(std::cos(th) * (1.0 - 1e-6)) : -2.0f;
+}
+
+// Sigma of the matched filter: the PSF's, broadened by the coarse-search
+// smoothing when one is set (Gaussians convolve by adding variances).
+float filter_sigma(const ndt_ctx* ctx, float psf_sigma) {
+  if (ctx->broaden <= 0.0f) return psf_sigma;
+  return (float)std::sqrt((double)psf_sigma * psf_sigma + (double)ctx->broaden * ctx->broaden);
 }
 
 void record(ndt_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
@@ -329,6 +337,9 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     if (!std::isfinite(m.mjd)) return fail(ctx, NDT_EINVAL, "exposure %d: epoch not finite", j);
     if (!(m.psf_sigma_px > 0.0f && m.psf_sigma_px <= 4.0f))
       return fail(ctx, NDT_EINVAL, "exposure %d: psf sigma %g outside (0, 4]", j, m.psf_sigma_px);
+    if (!(filter_sigma(ctx, m.psf_sigma_px) <= 4.0f))
+      return fail(ctx, NDT_EINVAL, "exposure %d: broadened filter sigma %g above 4 px", j,
+                  filter_sigma(ctx, m.psf_sigma_px));
     if (!variances && std::isnan(m.variance))
       return fail(ctx, NDT_EINVAL, "exposure %d: variance is NaN", j);
     if (!(std::isfinite(det) && det != 0.0)) return fail(ctx, NDT_EINVAL, "exposure %d: singular CD", j);
@@ -371,12 +382,12 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     max_tiles = std::max(max_tiles, e.tiles_x * tiles_y);
     PlaneJob& J = jobs[s];
     J.var_c = m.variance > 0.0f ? m.variance : 1.0f;
-    J.sigma = m.psf_sigma_px;
+    J.sigma = filter_sigma(ctx, m.psf_sigma_px);
     // unit-sum 1-D Gaussian window of the truncated PSF (FP64, rounded once)
-    J.R = (int)std::ceil(4.0 * (double)m.psf_sigma_px);
+    J.R = (int)std::ceil(4.0 * (double)J.sigma);
     {
       double w[2 * kMaxPsfRadius + 1], sum = 0.0;
-      const double s2 = 2.0 * (double)m.psf_sigma_px * (double)m.psf_sigma_px;
+      const double s2 = 2.0 * (double)J.sigma * (double)J.sigma;
       for (int k = -J.R; k <= J.R; ++k) sum += (w[k + J.R] = std::exp(-(double)(k * k) / s2));
       double sg2 = 0.0;
       for (int k = 0; k <= 2 * J.R; ++k) {
@@ -830,6 +841,14 @@ ndt_status ndt_set_launch(ndt_ctx* ctx, int32_t mode, int32_t orbit_tile, int32_
   }
   ctx->mode = mode;
   ctx->use_graph = use_graph ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_set_filter_broadening(ndt_ctx* ctx, float sigma_px) {
+  if (!ctx) return NDT_EINVAL;
+  if (!(sigma_px >= 0.0f) || !std::isfinite(sigma_px))
+    return fail(ctx, NDT_EINVAL, "filter broadening %g must be finite and >= 0", sigma_px);
+  ctx->broaden = sigma_px;
   return NDT_OK;
 }
 

@@ -62,6 +62,7 @@ _lib.ndt_predict_positions.argtypes = [_vp, _vp, _f64, _i64, _vp]
 _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
 _lib.ndt_set_offchip_test.argtypes = [_vp, _i32]
+_lib.ndt_set_filter_broadening.argtypes = [_vp, C.c_float]
 _lib.ndt_trim_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _i32, _vp, _vp]
 _lib.ndt_noise_mad.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_i64), _i32, _i32, _vp, _vp, _vp]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
@@ -195,6 +196,12 @@ def set_launch(ctx, mode, orbit_tile=64, exp_tile=16, use_graph=False):
     _check(ctx, _lib.ndt_set_launch(ctx, int(mode), int(orbit_tile), int(exp_tile), int(bool(use_graph))))
 
 
+def set_filter_broadening(ctx, sigma_px):
+    """Matched filter of the next load_exposures broadened by a Gaussian of
+    sigma_px (0: the plain filter)."""
+    _check(ctx, _lib.ndt_set_filter_broadening(ctx, float(sigma_px)))
+
+
 def set_offchip_test(ctx, enabled):
     _check(ctx, _lib.ndt_set_offchip_test(ctx, int(bool(enabled))))
 
@@ -292,6 +299,7 @@ def exported_symbols():
     return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
             "ndt_load_exposures", "ndt_stack_orbits", "ndt_topk_candidates",
             "ndt_predict_positions", "ndt_get_planes", "ndt_set_launch", "ndt_set_offchip_test",
+            "ndt_set_filter_broadening",
             "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
