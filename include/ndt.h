@@ -323,6 +323,15 @@ ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, in
 ndt_status ndt_vet(ndt_ctx *ctx, const float *params, const double *states, double t0,
                    int64_t n_orbits, const int64_t *cand_idx, int64_t n_cand, float *scores);
 
+/* Self-test of the scoring kernel's bounded waits (no counterpart in the
+   paper).  Runs the tensor-core CNN forward on one zero stamp with the MMAs
+   of its first layer withheld, so the mbarrier wait for them cannot complete:
+   after its iteration limit (about a second per wait; the self-test meets
+   two) the kernel records the timeout,
+   frees its tensor memory and returns.  Returns NDT_ETIMEOUT when that path
+   works (any other status means it did not); the context stays usable. */
+ndt_status ndt_selftest_wait_timeout(ndt_ctx *ctx);
+
 /*
  * topk_noalloc: the ranking of ndt_topk_candidates (k largest values, ties to
  * the lower index, NaN ranked with -inf) for callers that cannot let a

@@ -22,6 +22,10 @@ namespace {
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }   // every buffer of a context is freed with it
   cudaError_t ensure(size_t bytes) {
     if (bytes <= cap) return cudaSuccess;
     if (p) cudaFree(p);
@@ -300,9 +304,11 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->fam_exp_off, &c->fam_exp_pos, &c->item_off, &c->fam_order,
                     &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
                     &c->cand_stage, &c->stamp_pos, &c->stamp_f32, &c->stamp_bf16, &c->cnn_x,
-                    &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad};
+                    &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad,
+                    &c->trim_bits, &c->trim_nu, &c->trim_n, &c->mad_imgs, &c->mad_state,
+                    &c->mad_hist, &c->mad_stage};
   for (DevBuf* b : bufs) b->release();
-  delete c;
+  delete c;   // (the DevBuf destructors free anything not listed above)
 }
 
 const char* ndt_last_error(const ndt_ctx* c) { return c ? c->err.c_str() : g_create_error; }
@@ -961,6 +967,25 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
 }  // namespace
 
 extern "C" {
+
+ndt_status ndt_selftest_wait_timeout(ndt_ctx* ctx) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  const int64_t np = cnn_param_count();
+  NDT_CK(ctx->cnn_params.ensure(sizeof(float) * np), "self-test parameters");
+  NDT_CK(ctx->cnn_x.ensure(2 * 2 * 441), "self-test stamp");
+  NDT_CK(ctx->cnn_out.ensure(sizeof(float)), "self-test logit");
+  NDT_CK(cudaMemsetAsync(ctx->cnn_params.p, 0, sizeof(float) * np, ctx->stream), "memset");
+  NDT_CK(cudaMemsetAsync(ctx->cnn_x.p, 0, 2 * 2 * 441, ctx->stream), "memset");
+  NDT_CK(cudaMemsetAsync(cnn_err(ctx), 0, sizeof(int), ctx->stream), "memset");
+  NDT_CK(launch_cnn_forward_tc(ctx->cnn_params.as<float>(), ctx->cnn_x.as<__nv_bfloat16>(), 1,
+                               ctx->cnn_out.as<float>(), cnn_err(ctx), 1, ctx->stream,
+                               /*withhold_first_layer=*/1),
+         "self-test kernel");
+  ctx->launches += 1;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return check_cnn_err(ctx);
+}
 
 ndt_status ndt_noise_mad(ndt_ctx* ctx, const float* const* images, const int64_t* n_pixels,
                          int32_t n_images, int32_t max_rounds, float* median_out, float* sigma_out,

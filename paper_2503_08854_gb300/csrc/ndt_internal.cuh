@@ -610,7 +610,7 @@ cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32
                         float* nu_out, int32_t* n_out, float* psi_out, float* phi_out, int n_sms,
                         cudaStream_t st);
 cudaError_t launch_cnn_forward_tc(const float* th, const __nv_bfloat16* x, int64_t n, float* logits,
-                                  int* err, int n_sms, cudaStream_t st);
+                                  int* err, int n_sms, cudaStream_t st, int withhold_first_layer = 0);
 cudaError_t launch_cnn_backward(const float* th, const __nv_bfloat16* x, const float* labels,
                                 int64_t n, float* grad, float* loss_sum, float* a1_scratch,
                                 float* logits, int n_sms, cudaStream_t st);

@@ -63,6 +63,7 @@ _lib.ndt_get_planes.argtypes = [_vp, _i32, _vp, _vp]
 _lib.ndt_set_launch.argtypes = [_vp, _i32, _i32, _i32, _i32]
 _lib.ndt_set_offchip_test.argtypes = [_vp, _i32]
 _lib.ndt_set_filter_broadening.argtypes = [_vp, C.c_float]
+_lib.ndt_selftest_wait_timeout.argtypes = [_vp]
 _lib.ndt_trim_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _i32, _vp, _vp]
 _lib.ndt_noise_mad.argtypes = [_vp, C.POINTER(_vp), C.POINTER(_i64), _i32, _i32, _vp, _vp, _vp]
 _lib.ndt_autotune.argtypes = [_vp, _vp, _f64, _i64, _vp, _vp, _vp, _i32, _vp]
@@ -261,6 +262,11 @@ def vet(ctx, params, states_soa, t0, n_orbits, cand_idx, scores):
                              _ptr(cand_idx), int(len(cand_idx)), _ptr(scores)))
 
 
+def selftest_wait_timeout(ctx):
+    """Status of ndt_selftest_wait_timeout (ETIMEOUT when the bounded waits work)."""
+    return _lib.ndt_selftest_wait_timeout(ctx)
+
+
 def noise_mad(ctx, images, max_rounds=10):
     """Iterative-MAD noise estimate of each image (ndt_noise_mad).  ``images``:
     a sequence of FP32 numpy arrays or torch tensors (host or device).
@@ -303,4 +309,4 @@ def exported_symbols():
             "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
-            "ndt_trim_candidates", "ndt_noise_mad", "ndt_topk_noalloc"]
+            "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc"]

@@ -188,3 +188,16 @@ def test_trimmed_snr_cuts_artefact_false_positives(gpu):
     assert fa_snr > 0.2
     assert fa_trim < 0.5 * fa_snr
     assert fpr_trim < fpr_snr
+
+
+def test_bounded_wait_timeout_path(gpu):
+    """The scoring kernel's mbarrier waits are bounded: with the first
+    layer's MMAs withheld the wait expires, the kernel frees its tensor
+    memory and the call reports NDT_ETIMEOUT; the context stays usable."""
+    assert ndt.selftest_wait_timeout(gpu.ctx) == ndt.ETIMEOUT
+    xb, x64 = _bf16_batch(5, 20)
+    th = _params(6)
+    p = torch.as_tensor(th, dtype=torch.float32, device=gpu.dev)
+    z = vetting.logits(gpu.ctx, p, xb.to(gpu.dev)).cpu().numpy()
+    ref = V.forward(th.astype(np.float32).astype(np.float64), x64, bf16_operands=True)
+    np.testing.assert_allclose(z, ref, rtol=2e-3, atol=2e-3 * np.abs(ref).max())
