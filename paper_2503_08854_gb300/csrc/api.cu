@@ -177,8 +177,8 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   to_ecl(p0, e.p0);
   to_ecl(ax, e.ax);
   to_ecl(ay, e.ay);
-  e.crpix[0] = m.crpix[0];
-  e.crpix[1] = m.crpix[1];
+  e.crpix_h[0] = m.crpix[0] + 0.5;
+  e.crpix_h[1] = m.crpix[1] + 0.5;
   // FP32 copies for the off-chip test; ppr = largest singular value of
   // CD^-1 (px/deg) in px/rad: the TAN map's stretch at the tangent point
   for (int i = 0; i < 3; ++i) {

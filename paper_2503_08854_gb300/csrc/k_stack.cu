@@ -97,10 +97,10 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
   }
   w.t_prev = e.t;
   if (FP32_COPY) walk_fp32_copy(w, e.tf);
-  double rho[3], x, y;
+  double rho[3], xh, yh;
   apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
   int ix, iy;
-  if (project(e, rho, x, y) && nearest_pixel(e, x, y, ix, iy)) {
+  if (project_h(e, rho, xh, yh) && nearest_pixel(e, xh, yh, ix, iy)) {
     const float2 pv = gather_plane<PT>(planes, e, ix, iy);
     w.sp.add(pv.x);
     w.sf.add(pv.y);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(kBlock) k_predict(const double* __restrict__ s
         double rho[3];
         apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
         double px, py;
-        if (project(e, rho, px, py)) { x = px; y = py; }
+        if (project_h(e, rho, px, py)) { x = px - 0.5; y = py - 0.5; }
       }
     }
     out[0] = x;

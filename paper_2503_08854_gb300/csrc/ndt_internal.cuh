@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bitconv.cuh"
+
 namespace ndt {
 
 constexpr int kTile = 32;          // plane tile edge (pixels); tiles are 32 x 32
@@ -26,9 +28,9 @@ struct ExpDev {
   double t;          // epoch (days)
   double obs[3];     // observer, heliocentric ecliptic (AU)
   double p0[3];      // unit vector of the tangent point, ecliptic frame
-  double ax[3];      // x = crpix_x + (rho . ax) / (rho . p0)
-  double ay[3];      // y = crpix_y + (rho . ay) / (rho . p0)
-  double crpix[2];   // 0-based
+  double ax[3];      // x + 1/2 = crpix_h[0] + (rho . ax) / (rho . p0)
+  double ay[3];      // y + 1/2 = crpix_h[1] + (rho . ay) / (rho . p0)
+  double crpix_h[2]; // reference pixel (0-based) + 1/2: pixel i spans [i, i + 1) in x + 1/2
   int64_t plane_off; // first element of this exposure's plane
   int32_t W, H;
   int32_t tiles_x;   // ceil(W / 32)
@@ -77,40 +79,6 @@ struct CSum {
   }
   __device__ __forceinline__ float value() const { return __fadd_rn(s, c); }
 };
-
-// FP64 -> FP32 by truncation on the integer pipe (exponent rebias and
-// mantissa shift of the IEEE-754 bit patterns), so that the FP64 pipe, which
-// bounds the stacking kernel, executes no conversion instruction.  Relative
-// error < 2^-23; magnitudes below 2^-126 become 0, above FP32 range infinity
-// (NaN too).
-__device__ __forceinline__ float d2f_trunc(double d) {
-  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
-  const unsigned sign = hi & 0x80000000u;
-  const int ex = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
-  if (ex <= 0) return __uint_as_float(sign);
-  if (ex >= 255) return __uint_as_float(sign | 0x7F800000u);
-  return __uint_as_float(sign | ((unsigned)ex << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
-}
-
-// FP64 -> FP32 rounded to nearest (ties away from zero) on the integer pipe:
-// half an FP32 ulp is added to the FP64 bit pattern (a carry moves into the
-// exponent as it should), then the pattern is truncated.  Relative error
-// <= 2^-24, as for the hardware conversion.
-__device__ __forceinline__ float d2f_rn(double d) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(d) + (1ull << 28);
-  return d2f_trunc(__longlong_as_double((long long)b));
-}
-
-// FP32 -> FP64 exactly, on the integer pipe; subnormal FP32 values become 0,
-// infinities and NaNs stay so.
-__device__ __forceinline__ double f2d_exact(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
-  const unsigned eh = e == 0u ? 0u : (e == 255u ? 0x7FFu : e + 896u);   // 896 = 1023 - 127
-  const unsigned hi = sign | (eh << 20) | (e == 0u ? 0u : m >> 3);
-  const unsigned lo = e == 0u ? 0u : m << 29;
-  return __hiloint2double((int)hi, (int)lo);
-}
 
 // ---------------------------------------------------------------------------
 // FP64 reciprocal by Newton-Raphson refinement of an FP32 seed (the classical
@@ -423,26 +391,27 @@ __device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], 
 
 // TAN projection through the precomputed per-exposure rows (Calabretta &
 // Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
-// Returns false when cos c <= 0.
+// Gives the pixel coordinates shifted by one half, (x + 1/2, y + 1/2), so
+// that the nearest pixel is their floor.  Returns false when cos c <= 0.
 // The reciprocal of rho . p0 needs ~1e-12 relative accuracy (x within 1e-8 px
 // at 4096 px from CRPIX): one Newton step from the FP32 seed gives < 1.5e-14.
 // The cos c > 0 test is an FP32 compare (the threshold only keeps the
 // reciprocal in range).
-__device__ __forceinline__ bool project(const ExpDev& e, const double rho[3], double& x, double& y) {
+__device__ __forceinline__ bool project_h(const ExpDev& e, const double rho[3], double& xh, double& yh) {
   const double den = rho[0] * e.p0[0] + rho[1] * e.p0[1] + rho[2] * e.p0[2];
   if (!(d2f_trunc(den) > 1e-30f)) return false;
   const double inv = rcp_nr<1>(den);
-  x = fma(rho[0] * e.ax[0] + rho[1] * e.ax[1] + rho[2] * e.ax[2], inv, e.crpix[0]);
-  y = fma(rho[0] * e.ay[0] + rho[1] * e.ay[1] + rho[2] * e.ay[2], inv, e.crpix[1]);
+  xh = fma(rho[0] * e.ax[0] + rho[1] * e.ax[1] + rho[2] * e.ax[2], inv, e.crpix_h[0]);
+  yh = fma(rho[0] * e.ay[0] + rho[1] * e.ay[1] + rho[2] * e.ay[2], inv, e.crpix_h[1]);
   return true;
 }
 
-// Nearest pixel (pixel i spans [i - 1/2, i + 1/2)); false outside the image.
-// (the conversion saturates far outside the int range, which stays outside
-// the image; x and y are finite whenever project() succeeded)
-__device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double x, double y, int& ix, int& iy) {
-  ix = __double2int_rd(x + 0.5);
-  iy = __double2int_rd(y + 0.5);
+// Nearest pixel (pixel i spans [i - 1/2, i + 1/2)) from the shifted
+// coordinates of project_h; false outside the image.  The floor runs on the
+// integer pipe; coordinates beyond 2^30 give INT_MIN, outside every image.
+__device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double xh, double yh, int& ix, int& iy) {
+  ix = floor_to_int(xh);
+  iy = floor_to_int(yh);
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
 }
 
