@@ -40,13 +40,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # off-chip test removed), and the FP64-pipe thread instructions per computed
 # sample (conversions and compares included).  MBA: workload at 512 orbits per
 # family and 1024 x 1024 images; batched: 128 families and 512 x 512 images.
-# MBA: 8.637e7 computed samples, 48.48 DFMA + 38.80 DMUL + 8.33 DADD each;
-# batched: 2.037e8 computed samples, 54.74 DFMA + 36.79 DMUL + 7.78 DADD.
-FP64_PER_SAMPLE = {"mba": (144.1, 98.6), "batched": (154.1, 102.8)}
+# MBA: 8.637e7 computed samples, 48.48 DFMA + 38.80 DMUL + 6.33 DADD each;
+# batched: 2.037e8 computed samples, 54.74 DFMA + 36.79 DMUL + 5.89 DADD.
+FP64_PER_SAMPLE = {"mba": (142.1, 94.6), "batched": (152.2, 99.0)}
 # DRAM bytes (read + write) of one full-size persistent stack launch (BF16
 # planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
-# in a one-pass capture: MBA 1.86 GB + 71.8 MB, batched 3.54 GB + 274.5 MB.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.932e9, "batched": 3.814e9}
+# in a one-pass capture; None until taken for the current kernel.
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
 
 
 def parse():
