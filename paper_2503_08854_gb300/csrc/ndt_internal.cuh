@@ -170,7 +170,7 @@ struct OrbitConst {
   double series_dt;    // steps shorter than this use the truncated f/g series
   // FP32 copies for branch tests (compared on the FP32 pipe): the series
   // bound shrunk by 1e-6 so that truncated |dt| never passes it wrongly
-  float series_dt_f, half_period_f, abs_alpha_f;
+  float series_dt_f, half_period_f, alpha_f;
   // bounds along the whole conic for the off-chip test (FP32): |d^3 r/dt^3| / 6,
   // GM / (2 q^2) >= |acceleration| / 2, and the perihelion speed v_q >= |v|
   float jerk6, half_acc, vq;
@@ -207,7 +207,7 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
     oc.series_dt_f = (float)(oc.series_dt * (1.0 - 1e-6));
     oc.half_period_f = oc.half_period < 1e30 ? (float)oc.half_period : INFINITY;
-    oc.abs_alpha_f = (float)fabs(oc.alpha);
+    oc.alpha_f = (float)oc.alpha;
     // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
     // <= 4 GM v_q / q^3 anywhere on the conic (r >= q, |v| <= v_q).
     if (ph.force_free) {
@@ -238,36 +238,60 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
 //   gdot = 1 - u t^2/2 + u p t^3
 // Used only when dt^2 K <= 1e-7 (K bounds u, p^2 and |w| along the conic):
 // the neglected terms are then O((dt^2 K)^(5/2)) relative, and a sweep of
-// random conics at the bound against the universal-variable solver shows
-// relative errors of 6e-16, so the step is exact to FP64 rounding without a
-// Kepler solve (about an hour for main-belt orbits, seconds near a close
-// perihelion).  1/|r| of the new state starts from the first-order
-// prediction (1/r)(1 - p t), whose relative error is O(dt^2 K) <= 1e-7, and
-// takes two Newton steps y <- y (3 - x y^2)/2 (error ~ (3/2) e^2 per step,
-// so below 1e-20 after two).
+// random conics at the bound against a 40-digit universal-variable solution
+// shows relative errors of 1.6e-16 in position and 5e-16 in velocity, so the
+// step is exact to FP64 rounding without a Kepler solve (about an hour for
+// main-belt orbits, seconds near a close perihelion).
+//
+// Precision split.  Relative to 1, the t^2 terms are below 5e-8 and every
+// higher term below 3e-11 (f, g/t, gdot) or 3e-4 of -u t (fdot).  FP64 is
+// kept for -u t^2/2, -u t and 3 u p t^2/2 (the last because its error would
+// act on the velocity and grow over the following steps), and for the state
+// updates themselves (r' = r + (f-1) r + g v, v' = fdot r + v + (gdot-1) v,
+// so that the small parts are never added to 1 first).  The other terms are
+// formed in FP32, where their rounding (~1e-7 of terms below 3e-11) stays far
+// under FP64 rounding of the result; w comes from the vis-viva integral,
+// w = u (1 - alpha r).  The FP32 <-> FP64 conversions run on the integer
+// pipe (see bitconv.cuh), so the FP64 pipe sees 39 instructions per step.
+//
+// 1/|r| of the new state starts from the first-order prediction
+// y0 = (1/r)(1 - p t), whose relative error e0 = O(dt^2 K) <= 1e-7, and takes
+// one third-order step y = y0 (1 + e/2 + 3 e^2/8) with e = 1 - x y0^2
+// (remainder 5 e^3 / 16 < 1e-21; the e^2 term, below 4e-15, is formed in
+// FP32).
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void fg_series_step(const Phys& ph, double t, double r[3], double v[3],
-                                               double& rn, double& inv_r) {
+__device__ __forceinline__ void fg_series_step(const Phys& ph, const OrbitConst& oc, double t,
+                                               double r[3], double v[3], double& rn, double& inv_r) {
   const double ir2 = inv_r * inv_r;
   const double u = ph.gm * ir2 * inv_r;
   const double p = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ir2;
-  const double w = fma(v[0] * v[0] + v[1] * v[1] + v[2] * v[2], ir2, -u);
-  const double t2 = t * t, t3 = t2 * t;
-  const double c4 = u * fma(3.0, w, fma(-15.0 * p, p, u));     // u (3w - 15p^2 + u)
-  const double up = u * p;
-  const double f = 1.0 + fma(-0.5 * u, t2, fma(0.5 * up, t3, (c4 * kInv24) * (t2 * t2)));
-  const double g = t + fma(-u * kInv6, t3, 0.25 * up * (t2 * t2));
-  const double fdot = fma(-u, t, fma(1.5 * up, t2, (c4 * kInv6) * t3));
-  const double gdot = 1.0 + fma(-0.5 * u, t2, up * t3);
+  const double t2 = t * t;
+  const double A = u * (-0.5 * t2);                                  // -u t^2 / 2
+  // FP32 parts
+  const float tf = d2f_rn(t), uf = d2f_rn(u), pf = d2f_rn(p);
+  const float wf = uf * fmaf(-oc.alpha_f, d2f_rn(rn), 1.0f);          // u (1 - alpha r)
+  const float c4f = uf * fmaf(3.0f, wf, fmaf(-15.0f * pf, pf, uf));   // u (3w - 15p^2 + u)
+  const float upf = uf * pf;
+  const float t2f = tf * tf, t3f = t2f * tf, t4f = t2f * t2f;
+  const float Bf = fmaf(0.5f * upf, t3f, (c4f * (1.0f / 24.0f)) * t4f);   // f - 1 + u t^2/2
+  const float Gf = fmaf(-uf * (1.0f / 6.0f), t3f, (0.25f * upf) * t4f);  // g - t
+  const float Kf = (c4f * (1.0f / 6.0f)) * t3f;                          // c4 t^3 / 6
+  const float Lf = upf * t3f;                                            // gdot - 1 + u t^2/2
+  // FP64 parts
+  const double fm1 = A + f2d_exact(Bf);
+  const double g = t + f2d_exact(Gf);
+  const double fdot = fma(-u, t, fma(1.5 * (u * p), t2, f2d_exact(Kf)));
+  const double gdm1 = A + f2d_exact(Lf);
   double rr[3];
-  for (int i = 0; i < 3; ++i) rr[i] = fma(f, r[i], g * v[i]);
-  for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], gdot * v[i]);
+  for (int i = 0; i < 3; ++i) rr[i] = fma(fm1, r[i], fma(g, v[i], r[i]));
+  for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], fma(gdm1, v[i], v[i]));
   for (int i = 0; i < 3; ++i) r[i] = rr[i];
   const double x = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-  double y = inv_r * fma(-p, t, 1.0);
-#pragma unroll
-  for (int k = 0; k < 2; ++k) y = y * fma(-0.5 * x * y, y, 1.5);
+  const double y0 = inv_r * fma(-p, t, 1.0);
+  const double e = fma(-x, y0 * y0, 1.0);
+  const float ef = d2f_rn(e);
+  const double y = fma(y0, fma(0.5, e, f2d_exact(0.375f * ef * ef)), y0);
   inv_r = y;
   rn = x * y;
 }
@@ -303,7 +327,7 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   }
   const float adtf = fabsf(d2f_trunc(dt));   // |dt| truncated: never above |dt|
   if (adtf <= oc.series_dt_f) {
-    fg_series_step(ph, dt, r, v, rn, inv_r);
+    fg_series_step(ph, oc, dt, r, v, rn, inv_r);
     return 0;
   }
   // (reducing a step just under half a period changes nothing: rint gives 0 or +-1)
@@ -317,7 +341,7 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   const double si = sig0 * inv_r;
   double chi = u * fma(u, fma(-(u * kInv6), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
   const float chif = d2f_trunc(chi);
-  if (oc.abs_alpha_f * chif * chif > 0.25f || !(fabsf(chif) < 1e30f)) {
+  if (fabsf(oc.alpha_f) * chif * chif > 0.25f || !(fabsf(chif) < 1e30f)) {
     chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
   }
   int it;
