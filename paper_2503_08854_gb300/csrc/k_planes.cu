@@ -68,24 +68,42 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
   const int x0 = tx * kTile - RM, y0 = ty * kTile - RM;
   const float inv_vc = 1.0f / J.var_c;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < E; r += kThreads / 32) {          // rows by warps, columns by lanes
-    const int yy = y0 + r;
-    const bool row_in = yy >= 0 && yy < H;
-    for (int c = lane; c < E; c += 32) {
-      const int xx = x0 + c;
-      float a = 0.0f, w = 0.0f;
-      if (row_in && xx >= 0 && xx < W) {
-        const int64_t p = (int64_t)yy * W + xx;
-        const float I = __ldg(J.image + p);
+  // input tile: rows by warps, columns by lanes, with compile-time trip
+  // counts so that every load of a thread is issued before the first is used
+  // (a CTA lives a few microseconds: its loads must overlap, not queue)
+  constexpr int kWarps = kThreads / 32;
+  constexpr int RPW = (E + kWarps - 1) / kWarps, CPL = (E + 31) / 32;
+  float a[RPW][CPL], wv[RPW][CPL];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + kWarps * i, yy = y0 + r;
+    const bool row_in = r < E && yy >= 0 && yy < H;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j, xx = x0 + c;
+      const bool ok = row_in && c < E && xx >= 0 && xx < W;
+      const int64_t p = (int64_t)yy * W + xx;
+      a[i][j] = ok ? __ldg(J.image + p) : 0.0f;
+      wv[i][j] = (vplane && ok) ? __ldg(J.var + p) : 0.0f;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int r = warp + kWarps * i, yy = y0 + r;
+#pragma unroll
+    for (int j = 0; j < CPL; ++j) {
+      const int c = lane + 32 * j, xx = x0 + c;
+      if (r < E && c < E) {
         if (vplane) {
-          w = 1.0f / __ldg(J.var + p);
-          a = I * w;
+          // outside the image a = w = 0 (zero padding of both planes)
+          const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
+          const float w = ok ? 1.0f / wv[i][j] : 0.0f;
+          in[r * ES + c] = a[i][j] * w;
+          inw[r * ES + c] = w;
         } else {
-          a = I * inv_vc;
+          in[r * ES + c] = a[i][j] * inv_vc;
         }
       }
-      in[r * ES + c] = a;
-      if (vplane) inw[r * ES + c] = w;
     }
   }
   __syncthreads();

@@ -337,12 +337,18 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   const double a1 = fma(-alpha, rn, 1.0);            // 1 - alpha r0
   const double sdt = ph.sqrt_gm * dt;
   // third-order series of chi(dt): u - sig0 u^2/(2 r0) - u^3/6 (1/r0 - alpha - 3 sig0^2/r0^2)
-  const double u = sdt * inv_r;
-  const double si = sig0 * inv_r;
-  double chi = u * fma(u, fma(-(u * kInv6), fma(-3.0 * si, si, inv_r - alpha), -0.5 * si), 1.0);
-  const float chif = d2f_trunc(chi);
+  // with u = sqrt(GM) dt / r0, in FP32: the guess only starts the iteration,
+  // whose residual, stopping test and final correction are FP64 (its FP32
+  // rounding, ~1e-7 of chi, is a small part of the first correction)
+  const float irf = d2f_rn(inv_r);
+  const float uf = d2f_rn(sdt) * irf, sif = d2f_rn(sig0) * irf;
+  const float chif =
+      uf * fmaf(uf, fmaf(-uf * (1.0f / 6.0f), fmaf(-3.0f * sif, sif, irf - oc.alpha_f), -0.5f * sif), 1.0f);
+  double chi;
   if (fabsf(oc.alpha_f) * chif * chif > 0.25f || !(fabsf(chif) < 1e30f)) {
-    chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : u;   // far from the series' range
+    chi = alpha > 0.0 ? ph.sqrt_gm * alpha * dt : sdt * inv_r;   // far from the series' range
+  } else {
+    chi = f2d_exact(chif);
   }
   int it;
   for (it = 1; it <= kMaxKeplerIters; ++it) {
