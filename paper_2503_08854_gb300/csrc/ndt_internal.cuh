@@ -170,7 +170,7 @@ struct OrbitConst {
   double series_dt;    // steps shorter than this use the truncated f/g series
   // FP32 copies for branch tests (compared on the FP32 pipe): the series
   // bound shrunk by 1e-6 so that truncated |dt| never passes it wrongly
-  float series_dt_f, half_period_f, alpha_f;
+  float series_dt_f, tiny_dt_f, half_period_f, alpha_f;
   // bounds along the whole conic for the off-chip test (FP32): |d^3 r/dt^3| / 6,
   // GM / (2 q^2) >= |acceleration| / 2, and the perihelion speed v_q >= |v|
   float jerk6, half_acc, vq;
@@ -206,6 +206,7 @@ __device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r
     const double K = ph.gm / (q * q * q) + vq2 / (q * q);
     oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
     oc.series_dt_f = (float)(oc.series_dt * (1.0 - 1e-6));
+    oc.tiny_dt_f = (q > 0.0 && K > 0.0 && K < 1e300) ? (float)(sqrt(3e-10 / K) * (1.0 - 1e-6)) : 0.0f;
     oc.half_period_f = oc.half_period < 1e30 ? (float)oc.half_period : INFINITY;
     oc.alpha_f = (float)oc.alpha;
     // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
@@ -296,6 +297,48 @@ __device__ __forceinline__ void fg_series_step(const Phys& ph, const OrbitConst&
   rn = x * y;
 }
 
+// Very short steps, dt^2 K <= 3e-10 (back-to-back exposures: 90 s for a
+// main-belt orbit gives ~1e-10).  Then even u t^2/2 is below 1.5e-10 and its
+// FP32 rounding below 1e-17, so f - 1, g - t and gdot - 1 are formed wholly in
+// FP32 (p too: its error only reaches terms below 1e-12 of the step).  FP64 is
+// kept for -u t in fdot (an error there would act on the velocity and grow
+// over the following steps), for the state updates and for 1/|r|, which takes
+// one second-order step y0 (1 + e/2) from the first-order prediction
+// (e <= ~1e-9, remainder 3 e^2 / 8 < 1e-18).  26 FP64 instructions.
+__device__ __forceinline__ void fg_tiny_step(const Phys& ph, const OrbitConst& oc, double t,
+                                             double r[3], double v[3], double& rn, double& inv_r) {
+  const double ir2 = inv_r * inv_r;
+  const double u = ph.gm * ir2 * inv_r;
+  const float irf = d2f_rn(inv_r), tf = d2f_rn(t), uf = d2f_rn(u);
+  const float rvf = fmaf(d2f_rn(r[0]), d2f_rn(v[0]),
+                         fmaf(d2f_rn(r[1]), d2f_rn(v[1]), d2f_rn(r[2]) * d2f_rn(v[2])));
+  const float pf = rvf * irf * irf;
+  const float upf = uf * pf;
+  const float t2f = tf * tf, t3f = t2f * tf;
+  const float Af = -0.5f * uf * t2f;                                  // -u t^2 / 2
+  const float fm1f = fmaf(0.5f * upf, t3f, Af);                       // f - 1
+  const float gm1f = -uf * (1.0f / 6.0f) * t3f;                       // g - t
+  // fdot + u t: 3 u p t^2/2 + u (3w - 15p^2 + u) t^3/6 (the last is ~dt^2 K of
+  // u t, with the same sign at every step: kept so the velocity does not drift)
+  const float wf = uf * fmaf(-oc.alpha_f, d2f_rn(rn), 1.0f);
+  const float c4f = uf * fmaf(3.0f, wf, fmaf(-15.0f * pf, pf, uf));
+  const float kf = fmaf(1.5f * upf, t2f, (c4f * (1.0f / 6.0f)) * t3f);
+  const float gdm1f = fmaf(upf, t3f, Af);                             // gdot - 1
+  const double fm1 = f2d_exact(fm1f), g = t + f2d_exact(gm1f);
+  const double fdot = fma(-u, t, f2d_exact(kf));
+  const double gdm1 = f2d_exact(gdm1f);
+  double rr[3];
+  for (int i = 0; i < 3; ++i) rr[i] = fma(fm1, r[i], fma(g, v[i], r[i]));
+  for (int i = 0; i < 3; ++i) v[i] = fma(fdot, r[i], fma(gdm1, v[i], v[i]));
+  for (int i = 0; i < 3; ++i) r[i] = rr[i];
+  const double x = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  const double y0 = fma(inv_r, f2d_exact(-pf * tf), inv_r);            // (1/r)(1 - p t)
+  const double e = fma(-x, y0 * y0, 1.0);
+  const double y = fma(0.5 * y0, e, y0);
+  inv_r = y;
+  rn = x * y;
+}
+
 // ---------------------------------------------------------------------------
 // One two-body step of length dt (universal-variable formulation), updating
 // the state (r, v) in place together with |r| and 1/|r|.
@@ -327,7 +370,10 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
   }
   const float adtf = fabsf(d2f_trunc(dt));   // |dt| truncated: never above |dt|
   if (adtf <= oc.series_dt_f) {
-    fg_series_step(ph, oc, dt, r, v, rn, inv_r);
+    if (adtf <= oc.tiny_dt_f)
+      fg_tiny_step(ph, oc, dt, r, v, rn, inv_r);
+    else
+      fg_series_step(ph, oc, dt, r, v, rn, inv_r);
     return 0;
   }
   // (reducing a step just under half a period changes nothing: rint gives 0 or +-1)

@@ -161,8 +161,10 @@ def test_positions_mixed_orbit_classes_long_span(gpu):
 
 
 def test_chained_short_steps_track_the_oracle_tightly(gpu):
-    """Hundreds of chained steps, most of them short enough for the f/g
-    series (ten visits 15 min apart per night for 30 nights): with light time
+    """Hundreds of chained steps of all three kinds: 90 s between the two
+    snaps of a visit (the shortest-step series), 15 min between five visits
+    of a night (the f/g series) and a day between nights (the universal-
+    variable step), for 30 nights.  With light time
     off on both sides, NEO, main-belt, Kuiper-belt and hyperbolic positions
     at 0.2 arcsec pixels stay within 1e-5 px of the oracle's direct FP64
     propagation from the epoch, 100x inside the general position bound.  A
@@ -172,8 +174,9 @@ def test_chained_short_steps_track_the_oracle_tightly(gpu):
     n_obj = 24
     states = _mixed_population(rng, n_obj)
     nights = np.arange(30.0)
-    mjd = (60200.0 + nights[:, None] + 0.1 + np.arange(10)[None, :] * (15.0 / 1440.0)
-           + rng.uniform(0, 60.0 / 86400.0, (30, 10))).ravel()
+    visit = np.repeat(np.arange(5), 2) * (15.0 / 1440.0) + np.tile([0.0, 90.0 / 86400.0], 5)
+    mjd = (60200.0 + nights[:, None] + 0.1 + visit[None, :]
+           + rng.uniform(0, 20.0 / 86400.0, (30, 1))).ravel()
     n_exp = mjd.size
     t0 = 60215.0
     obs = synth.observer_position(mjd, t0, 0.3)
