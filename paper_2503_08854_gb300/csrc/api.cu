@@ -181,10 +181,20 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   e.crpix_h[1] = m.crpix[1] + 0.5;
   // FP32 copies for the off-chip test; ppr = largest singular value of
   // CD^-1 (px/deg) in px/rad: the TAN map's stretch at the tangent point
+  // (high parts by the device's own split, so both sides use one rounding)
   for (int i = 0; i < 3; ++i) {
-    e.p0_f[i] = (float)e.p0[i];
-    e.ax_f[i] = (float)e.ax[i];
-    e.ay_f[i] = (float)e.ay[i];
+    const dfloat p = split_df(e.p0[i]), a = split_df(e.ax[i]), b = split_df(e.ay[i]);
+    e.p0_f[i] = p.h;
+    e.p0_l[i] = p.l;
+    e.ax_f[i] = a.h;
+    e.ax_l[i] = a.l;
+    e.ay_f[i] = b.h;
+    e.ay_l[i] = b.l;
+  }
+  for (int i = 0; i < 2; ++i) {
+    const dfloat c = split_df(e.crpix_h[i]);
+    e.crh_h[i] = c.h;
+    e.crh_l[i] = c.l;
   }
   e.crpix_f[0] = (float)m.crpix[0];
   e.crpix_f[1] = (float)m.crpix[1];

@@ -1,0 +1,132 @@
+// Double-float arithmetic: a value carried as an unevaluated sum hi + lo of
+// two FP32 numbers (|lo| <= ulp(hi)/2), about 48 significant bits, with
+// error-free transformations built on the FP32 FMA (Dekker 1971; Knuth, TAOCP
+// vol. 2, sec. 4.2.2; Ogita, Rump & Oishi 2005).  The stacking kernel uses it
+// for the TAN projection: a one-shot, non-accumulating computation whose
+// nearest-pixel decision needs ~1e-9 px, which 48 bits give, while every FP64
+// instruction it would otherwise take is on the pipe that bounds the kernel.
+// Compiles for the host too, where tests check it against long double.
+#pragma once
+
+#include <cmath>
+
+#include "bitconv.cuh"
+
+namespace ndt {
+
+struct dfloat {
+  float h, l;
+};
+
+// correctly rounded FP32 operations that the compiler may not contract
+NDT_HD float add_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fadd_rn(a, b);
+#else
+  volatile float s = a + b;
+  return s;
+#endif
+}
+NDT_HD float sub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fsub_rn(a, b);
+#else
+  volatile float s = a - b;
+  return s;
+#endif
+}
+NDT_HD float mul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fmul_rn(a, b);
+#else
+  volatile float s = a * b;
+  return s;
+#endif
+}
+NDT_HD float fma_rn(float a, float b, float c) {
+#ifdef __CUDA_ARCH__
+  return __fmaf_rn(a, b, c);
+#else
+  return std::fmaf(a, b, c);
+#endif
+}
+NDT_HD float rcp_approx(float a) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(a);
+#else
+  return 1.0f / a;
+#endif
+}
+
+// s + e = a + b exactly (Knuth's two-sum)
+NDT_HD dfloat two_sum(float a, float b) {
+  const float s = add_rn(a, b);
+  const float bb = sub_rn(s, a);
+  const float e = add_rn(sub_rn(a, sub_rn(s, bb)), sub_rn(b, bb));
+  return {s, e};
+}
+// s + e = a + b exactly when |a| >= |b| or a == 0
+NDT_HD dfloat fast_two_sum(float a, float b) {
+  const float s = add_rn(a, b);
+  return {s, sub_rn(b, sub_rn(s, a))};
+}
+// p + e = a b exactly (FMA two-product)
+NDT_HD dfloat two_prod(float a, float b) {
+  const float p = mul_rn(a, b);
+  return {p, fma_rn(a, b, -p)};
+}
+
+// An FP64 value as hi + lo on the integer pipe: hi = d2f_rn(v) (24 bits of
+// the significand, rounded) and lo = the remaining 29 bits of the significand
+// rounded to FP32, so hi + lo = v to 2^-48 relative.  lo is 0 when v is zero,
+// below 2^-73 in magnitude (negligible here) or outside the FP32 range.
+NDT_HD dfloat split_df(double v) {
+  const float h = d2f_rn(v);
+  const unsigned hi = hi_word(v), lo32 = lo_word(v);
+  const int ex = (int)((hi >> 20) & 0x7FFu);
+  const int r29 = (int)(lo32 & 0x1FFFFFFFu);                 // significand bits below hi's
+  const int rem = r29 >= (1 << 28) ? r29 - (1 << 29) : r29;  // d2f_rn rounded up at >= half
+  const int se = ex - 1075 + 127;                           // FP32 exponent of 2^(ex - 1075)
+  float l = 0.0f;
+  if (ex != 0 && se > 0 && se < 255) l = (float)rem * float_of_bits((unsigned)se << 23);
+  if (hi & 0x80000000u) l = -l;
+  return {h, l};
+}
+
+// a . b for 3-vectors of double-floats; error ~2^-47 sum |a_i b_i|
+NDT_HD dfloat df_dot3(const dfloat a[3], const dfloat b[3]) {
+  dfloat p[3];
+  float low = 0.0f;
+  for (int i = 0; i < 3; ++i) {
+    p[i] = two_prod(a[i].h, b[i].h);
+    low = fma_rn(a[i].h, b[i].l, fma_rn(a[i].l, b[i].h, add_rn(low, p[i].l)));
+  }
+  const dfloat s1 = two_sum(p[0].h, p[1].h);
+  const dfloat s2 = two_sum(s1.h, p[2].h);
+  return fast_two_sum(s2.h, add_rn(low, add_rn(s1.l, s2.l)));
+}
+
+// n / d (d != 0); relative error ~2^-46
+NDT_HD dfloat df_div(dfloat n, dfloat d) {
+  const float r = rcp_approx(d.h);
+  const float q1 = mul_rn(n.h, r);
+  const dfloat p = two_prod(q1, d.h);
+  // n - q1 d: n.h - p.h is exact (Sterbenz), the rest are small corrections
+  const float rem = fma_rn(-q1, d.l, sub_rn(add_rn(sub_rn(n.h, p.h), n.l), p.l));
+  return fast_two_sum(q1, mul_rn(rem, r));
+}
+
+NDT_HD dfloat df_add(dfloat a, dfloat b) {
+  const dfloat s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, add_rn(s.l, add_rn(a.l, b.l)));
+}
+
+// floor(hi + lo) for a normalised pair: floor(hi), one lower when hi is an
+// integer and lo < 0; INT_MIN when |hi| >= 2^30 or not finite
+NDT_HD int df_floor(dfloat x) {
+  if (!(std::fabs(x.h) < 1073741824.0f)) return INT_MIN;
+  const float f = std::floor(x.h);
+  return (int)f - ((f == x.h && x.l < 0.0f) ? 1 : 0);
+}
+
+}  // namespace ndt

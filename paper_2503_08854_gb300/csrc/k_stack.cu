@@ -97,10 +97,10 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
   }
   w.t_prev = e.t;
   if (FP32_COPY) walk_fp32_copy(w, e.tf);
-  double rho[3], xh, yh;
+  double rho[3];
   apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
   int ix, iy;
-  if (project_h(e, rho, xh, yh) && nearest_pixel(e, xh, yh, ix, iy)) {
+  if (pixel_of(e, rho, ix, iy)) {
     const float2 pv = gather_plane<PT>(planes, e, ix, iy);
     w.sp.add(pv.x);
     w.sf.add(pv.y);

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "bitconv.cuh"
+#include "dfloat.cuh"
 
 namespace ndt {
 
@@ -42,9 +43,11 @@ struct ExpDev {
   float obs_f[3], p0_f[3], ax_f[3], ay_f[3], crpix_f[2];
   float ppr;         // largest pixel stretch per radian at the tangent point (||CD^-1|| in px/rad)
   float cos_far;     // cos(largest off-axis angle of the chip + 0.01 rad), or -2 (never)
-  float pad2_;
+  // low parts of p0, ax, ay (their high parts are p0_f, ax_f, ay_f) and
+  // crpix_h as a high/low pair: the double-float projection of the stack
+  float p0_l[3], ax_l[3], ay_l[3], crh_h[2], crh_l[2];
 };
-static_assert(sizeof(ExpDev) == 224 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
+static_assert(sizeof(ExpDev) == 272 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
@@ -488,6 +491,26 @@ __device__ __forceinline__ bool project_h(const ExpDev& e, const double rho[3], 
 __device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double xh, double yh, int& ix, int& iy) {
   ix = floor_to_int(xh);
   iy = floor_to_int(yh);
+  return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
+}
+
+// Nearest pixel of a topocentric vector through the TAN projection in
+// double-float arithmetic (the FP64 vector split into FP32 pairs on the
+// integer pipe, ~48-bit dot products and quotient): the same x + 1/2 and
+// y + 1/2 as project_h to ~2e-8 px at 0.2 arcsec pixels (host check against
+// long double), with no FP64 instruction.  False when cos c <= 0 or outside
+// the image.
+__device__ __forceinline__ bool pixel_of(const ExpDev& e, const double rho[3], int& ix, int& iy) {
+  const dfloat R[3] = {split_df(rho[0]), split_df(rho[1]), split_df(rho[2])};
+  const dfloat P[3] = {{e.p0_f[0], e.p0_l[0]}, {e.p0_f[1], e.p0_l[1]}, {e.p0_f[2], e.p0_l[2]}};
+  const dfloat den = df_dot3(R, P);
+  if (!(den.h > 1e-30f)) return false;
+  const dfloat AX[3] = {{e.ax_f[0], e.ax_l[0]}, {e.ax_f[1], e.ax_l[1]}, {e.ax_f[2], e.ax_l[2]}};
+  const dfloat AY[3] = {{e.ay_f[0], e.ay_l[0]}, {e.ay_f[1], e.ay_l[1]}, {e.ay_f[2], e.ay_l[2]}};
+  const dfloat xh = df_add({e.crh_h[0], e.crh_l[0]}, df_div(df_dot3(R, AX), den));
+  const dfloat yh = df_add({e.crh_h[1], e.crh_l[1]}, df_div(df_dot3(R, AY), den));
+  ix = df_floor(xh);
+  iy = df_floor(yh);
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
 }
 
