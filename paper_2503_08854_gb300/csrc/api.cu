@@ -147,6 +147,12 @@ void set_default_phys(ndt_ctx* c, double gm, double cl, double eps) {
   c->ph.inv_c = cl > 0.0 ? (float)(1.0 / cl) : 0.0f;
   c->ph.inv_c2 = cl > 0.0 ? (float)(1.0 / (cl * cl)) : 0.0f;
   c->ph.gm_f = gm > 0.0 ? (float)gm : 0.0f;
+  {
+    const dfloat ic = split_df(cl > 0.0 ? 1.0 / cl : 0.0);
+    c->ph.inv_c = ic.h;
+    c->ph.inv_c_l = ic.l;
+    c->ph.inv_c3 = cl > 0.0 ? (float)(1.0 / (cl * cl * cl)) : 0.0f;
+  }
   c->obliquity = eps;
 }
 
@@ -386,7 +392,11 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     for (int i = 0; i < 3; ++i) e.obs[i] = m.obs_xyz[i];
     derive_projection(m, ctx->obliquity, e);
     e.tf = (float)(m.mjd - ctx->t_ref);
-    for (int i = 0; i < 3; ++i) e.obs_f[i] = (float)m.obs_xyz[i];
+    for (int i = 0; i < 3; ++i) {
+      const dfloat o = split_df(m.obs_xyz[i]);
+      e.obs_f[i] = o.h;
+      e.obs_l[i] = o.l;
+    }
     e.W = m.width;
     e.H = m.height;
     e.tiles_x = (m.width + kTile - 1) / kTile;

@@ -97,8 +97,8 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
   }
   w.t_prev = e.t;
   if (FP32_COPY) walk_fp32_copy(w, e.tf);
-  double rho[3];
-  apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
+  dfloat rho[3];
+  apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rho);
   int ix, iy;
   if (pixel_of(e, rho, ix, iy)) {
     const float2 pv = gather_plane<PT>(planes, e, ix, iy);
@@ -240,8 +240,10 @@ __global__ void __launch_bounds__(kBlock) k_predict(const double* __restrict__ s
         atomicAdd(counters + 1, 1ull);
       } else {
         w.t_prev = e.t;
-        double rho[3];
-        apparent_rho(ph, w.r, w.v, w.inv_r, e.obs, rho);
+        dfloat rd[3];
+        apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rd);
+        const double rho[3] = {f2d_exact(rd[0].h) + f2d_exact(rd[0].l), f2d_exact(rd[1].h) + f2d_exact(rd[1].l),
+                               f2d_exact(rd[2].h) + f2d_exact(rd[2].l)};
         double px, py;
         if (project_h(e, rho, px, py)) { x = px - 0.5; y = py - 0.5; }
       }

@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
         atomicAdd(counters + 1, 1ull);
       } else {
         t_prev = e.t;
-        double rho[3];
+        dfloat rho[3];
         int ix, iy;
-        apparent_rho(ph, r, v, inv_r, e.obs, rho);
+        apparent_rho_df(ph, r, v, inv_r, e, rho);
         if (pixel_of(e, rho, ix, iy)) p = make_int2(ix, iy);
       }
     }

@@ -46,8 +46,10 @@ struct ExpDev {
   // low parts of p0, ax, ay (their high parts are p0_f, ax_f, ay_f) and
   // crpix_h as a high/low pair: the double-float projection of the stack
   float p0_l[3], ax_l[3], ay_l[3], crh_h[2], crh_l[2];
+  float obs_l[3];    // low parts of obs (high parts: obs_f), for the double-float light time
+  float pad3_;
 };
-static_assert(sizeof(ExpDev) == 272 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
+static_assert(sizeof(ExpDev) == 288 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
@@ -58,6 +60,8 @@ struct Phys {
   float inv_c2;     // 1 / c^2
   float gm_f;       // GM_sun in FP32 (light-time acceleration term)
   int32_t force_free;
+  float inv_c_l;    // 1/c - inv_c: 1/c as the double-float pair (inv_c, inv_c_l)
+  float inv_c3;     // 1 / c^3
 };
 
 // Plane storage type tags.
@@ -439,33 +443,44 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
 }
 
 // ---------------------------------------------------------------------------
-// Light-time corrected topocentric vector.  With (r, v) the geometric state
-// at the exposure epoch and d = r - r_obs, the emitted position is expanded
-// to second order in the light time tau:
+// Light-time corrected topocentric vector, in double-float arithmetic (FP32
+// pairs, ~48 bits; see dfloat.cuh).  With (r, v) the geometric state at the
+// exposure epoch and d = r - r_obs, the emitted position is expanded to
+// second order in the light time tau:
 //   rho = d - tau v - (tau^2 / 2) GM r / |r|^3
-// (the third-order term is below 1e-11 AU for every orbit class in the
-// workloads).  tau solves tau = |rho| / c; starting from tau0 = |d| / c, one
-// fixed-point step gives tau1 = tau0 - (d . v) / c^2 to relative accuracy
-// (v/c)^2 ~ 1e-8, which moves rho by under 1e-11 AU.  tau only needs ~1e-7
-// relative accuracy, so it is carried in FP32; rho itself is FP64.
+// (the third-order term is below 1e-13 AU for main-belt orbits and 1e-11 AU
+// for every orbit class in the workloads).  tau is the root of
+// |d - tau v| = c tau expanded to second order in v/c:
+//   tau = |d|/c - (d.v)/c^2 + (|d| v^2 + (d.v)^2 / |d|) / (2 c^3),
+// whose next term is ~(v/c)^3 ~ 2e-13 relative.  d, |d|^2, |d|, |d|/c and
+// tau v are double-float (tau to ~1e-14 relative), the corrections FP32, and
+// the state enters through the integer-pipe split of its FP64 values: no FP64
+// instruction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void apparent_rho(const Phys& ph, const double r[3], const double v[3],
-                                             double inv_r, const double obs[3], double rho[3]) {
-  const double d[3] = {r[0] - obs[0], r[1] - obs[1], r[2] - obs[2]};
-  if (ph.inv_c == 0.0f) {
-    rho[0] = d[0]; rho[1] = d[1]; rho[2] = d[2];
-    return;
+__device__ __forceinline__ void apparent_rho_df(const Phys& ph, const double r[3], const double v[3],
+                                                double inv_r, const ExpDev& e, dfloat rho[3]) {
+  dfloat R[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R[i] = split_df(r[i]);
+    rho[i] = df_add(R[i], {-e.obs_f[i], -e.obs_l[i]});     // d
   }
-  // |d|^2, d.v and the products t v, h r stay FP64: at 0.2 arcsec pixels the
-  // nearest-pixel decision needs rho to ~1e-12 AU, which an FP32 correction
-  // (~1e-4 AU to 2^-24) does not give.  The conversions run on the integer pipe.
-  const double dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-  const double dv = d[0] * v[0] + d[1] * v[1] + d[2] * v[2];
-  const float tau = fmaf(-d2f_rn(dv), ph.inv_c2, __fsqrt_rn(d2f_rn(dd)) * ph.inv_c);
+  if (ph.inv_c == 0.0f) return;
+  dfloat V[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) V[i] = split_df(v[i]);
+  const dfloat dist = df_sqrt(df_dot3(rho, rho));
+  const float dv = fmaf(rho[0].h, V[0].h, fmaf(rho[1].h, V[1].h, rho[2].h * V[2].h));
+  const float v2 = fmaf(V[0].h, V[0].h, fmaf(V[1].h, V[1].h, V[2].h * V[2].h));
+  const float corr = fmaf(-dv, ph.inv_c2, 0.5f * ph.inv_c3 * fmaf(dist.h, v2, dv * dv / dist.h));
+  const dfloat tau = df_add(df_mul(dist, {ph.inv_c, ph.inv_c_l}), {corr, 0.0f});
   const float irf = d2f_rn(inv_r);
-  const float hf = ph.force_free ? 0.0f : -0.5f * ph.gm_f * irf * irf * irf * tau * tau;
-  const double t = f2d_exact(tau), h = f2d_exact(hf);
-  for (int i = 0; i < 3; ++i) rho[i] = fma(h, r[i], fma(-t, v[i], d[i]));
+  const float hf = ph.force_free ? 0.0f : -0.5f * ph.gm_f * irf * irf * irf * tau.h * tau.h;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const dfloat tv = df_mul(tau, V[i]);
+    rho[i] = df_add(df_add(rho[i], {-tv.h, -tv.l}), {hf * R[i].h, 0.0f});
+  }
 }
 
 // TAN projection through the precomputed per-exposure rows (Calabretta &
@@ -494,14 +509,13 @@ __device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double xh, double
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
 }
 
-// Nearest pixel of a topocentric vector through the TAN projection in
-// double-float arithmetic (the FP64 vector split into FP32 pairs on the
-// integer pipe, ~48-bit dot products and quotient): the same x + 1/2 and
+// Nearest pixel of a topocentric vector (double-float, from apparent_rho_df)
+// through the TAN projection in double-float arithmetic (~48-bit dot
+// products and quotient): the same x + 1/2 and
 // y + 1/2 as project_h to ~2e-8 px at 0.2 arcsec pixels (host check against
 // long double), with no FP64 instruction.  False when cos c <= 0 or outside
 // the image.
-__device__ __forceinline__ bool pixel_of(const ExpDev& e, const double rho[3], int& ix, int& iy) {
-  const dfloat R[3] = {split_df(rho[0]), split_df(rho[1]), split_df(rho[2])};
+__device__ __forceinline__ bool pixel_of(const ExpDev& e, const dfloat R[3], int& ix, int& iy) {
   const dfloat P[3] = {{e.p0_f[0], e.p0_l[0]}, {e.p0_f[1], e.p0_l[1]}, {e.p0_f[2], e.p0_l[2]}};
   const dfloat den = df_dot3(R, P);
   if (!(den.h > 1e-30f)) return false;
