@@ -34,19 +34,24 @@ UNIT = "samples/s"
 # FP64 peak of one GB300 derived from unit counts and clock: 152 SMs x 2 FP64
 # FMA per SM per clock x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# The stack kernel's bound: the FP64 pipe issues 2 thread-instructions per SM
+# per clock (152 SMs, 2.07 GHz), 629.3 G/s.  The roofline fraction is the
+# FP64-pipe time the launch needs (instructions per computed sample x computed
+# samples / that rate) over its measured time.
+FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 # FP64 flops executed per computed (orbit, exposure) sample by the stack
 # kernel, from ncu instruction counters (DFMA x 2 + DADD + DMUL) over the
 # samples whose FP64 work ran in the captured launch (samples minus those the
 # off-chip test removed), and the FP64-pipe thread instructions per computed
 # sample (conversions and compares included).  MBA: workload at 512 orbits per
 # family and 1024 x 1024 images; batched: 128 families and 512 x 512 images.
-# MBA: 8.637e7 computed samples, 48.48 DFMA + 38.80 DMUL + 6.33 DADD each;
-# batched: 2.037e8 computed samples, 54.74 DFMA + 36.79 DMUL + 5.89 DADD.
-FP64_PER_SAMPLE = {"mba": (142.1, 94.6), "batched": (152.2, 99.0)}
+# MBA: 8.637e7 computed samples, 24.21 DFMA + 12.86 DMUL + 1.99 DADD each;
+# batched: 2.037e8 computed samples, 32.06 DFMA + 18.23 DMUL + 2.04 DADD.
+FP64_PER_SAMPLE = {"mba": (63.3, 39.6), "batched": (84.4, 53.3)}
 # DRAM bytes (read + write) of one full-size persistent stack launch (BF16
 # planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
-# in a one-pass capture; None until taken for the current kernel.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": None, "batched": None}
+# in a one-pass capture: MBA 1.861 GB + 71.6 MB, batched 3.526 GB + 272.9 MB.
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.9326e9, "batched": 3.7989e9}
 
 
 def parse():
@@ -379,9 +384,13 @@ def noise_rate(device, stream, imgs):
 
 
 def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
-    """Same steps through the public API with pinned HOST inputs and outputs:
-    the H2D copies of images and orbit states and the D2H read of the top-k
-    are inside the timed region."""
+    """Same steps through the public API with pinned HOST inputs and outputs.
+    Every step copies its images and orbit states from pinned host memory and
+    reads its top-k back to the host, all inside the timed region.  Steps
+    alternate between two contexts (the form's and a second one with the same
+    launch configuration on its own stream), as a survey pipeline would: while
+    one context stacks step i, the other loads step i+1's images, so the
+    host-to-device copies overlap the stack kernel."""
     import torch
     from paper_2503_08854_gb300 import ndt
     n = states.shape[1]
@@ -391,49 +400,62 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
     ndt.stack_orbits(ctx, states, sky.t0, n, families=sky.fam_dev)
     ndt.topk_candidates(ctx, k, ref_idx)
     ref_idx = ref_idx.cpu().numpy()
-    h_imgs = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
-    h_imgs.copy_(imgs)
-    h_states = torch.empty(states.shape, dtype=states.dtype, pin_memory=True)
-    h_states.copy_(states)
-    torch.cuda.synchronize(device)
-    h_idx = torch.empty(k, dtype=torch.int64, pin_memory=True)
-    h_val = torch.empty(k, dtype=torch.float32, pin_memory=True)
-    np_imgs = h_imgs.numpy()
-    np_states = h_states.numpy()
+    st = ndt.get_stats(ctx)
+    stream2 = torch.cuda.Stream(device=device)
+    ctx2 = ndt.create(device.index, stream2)
+    try:
+        if form.mode == "persistent":
+            ndt.set_launch(ctx2, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"], use_graph=form.graph)
+        h_imgs = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
+        h_imgs.copy_(imgs)
+        h_states = torch.empty(states.shape, dtype=states.dtype, pin_memory=True)
+        h_states.copy_(states)
+        torch.cuda.synchronize(device)
+        # untimed: the host link's rate for this very buffer, for context
+        scratch = torch.empty_like(imgs)
+        link = []
+        for _ in range(3):
+            t = time.perf_counter()
+            scratch.copy_(h_imgs, non_blocking=True)
+            torch.cuda.synchronize(device)
+            link.append(time.perf_counter() - t)
+        del scratch
+        torch.cuda.empty_cache()
+        link_gbs = h_imgs.numel() * 4 / min(link) / 1e9
+        h_idx = [torch.empty(k, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+        h_val = [torch.empty(k, dtype=torch.float32, pin_memory=True) for _ in range(2)]
+        np_imgs = h_imgs.numpy()
+        np_states = h_states.numpy()
+        ctxs = (ctx, ctx2)
 
-    parts = []
+        def run(n_steps):
+            ndt.load_exposures(ctxs[0], sky.ex, np_imgs, plane_dtype=form.plane)
+            for i in range(n_steps):
+                c = ctxs[i % 2]
+                ndt.stack_orbits(c, np_states, sky.t0, n, families=sky.families)   # returns at once
+                if i + 1 < n_steps:                                                 # overlaps the stack
+                    ndt.load_exposures(ctxs[(i + 1) % 2], sky.ex, np_imgs, plane_dtype=form.plane)
+                ndt.topk_candidates(c, k, h_idx[i % 2].numpy(), h_val[i % 2].numpy())
+            return (n_steps - 1) % 2
 
-    def step():
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        ev[0].record(stream)
-        ndt.load_exposures(ctx, sky.ex, np_imgs, plane_dtype=form.plane)
-        ev[1].record(stream)
-        ndt.stack_orbits(ctx, np_states, sky.t0, n, families=sky.families)
-        ev[2].record(stream)
-        ndt.topk_candidates(ctx, k, h_idx.numpy(), h_val.numpy())
-        parts.append(ev)
-
-    for _ in range(max(1, args.warmup)):
-        step()
-    barrier()
-    torch.cuda.synchronize(device)
-    parts.clear()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    torch.cuda.synchronize(device)
-    dt = (time.perf_counter() - t0) / args.steps
+        run(max(1, args.warmup))
+        barrier()
+        torch.cuda.synchronize(device)
+        t0 = time.perf_counter()
+        last = run(args.steps)
+        torch.cuda.synchronize(device)
+        dt = (time.perf_counter() - t0) / args.steps
+    finally:
+        ndt.destroy(ctx2)
     h2d = int(h_imgs.numel() * 4 + h_states.numel() * 8)
     d2h = int(k * 12)
-    load_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in parts)
-    stack_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in parts)
-    got = np.array(h_idx.numpy())          # a copy: every figure below is of the same ranking
+    got = np.array(h_idx[last].numpy())      # a copy: every figure below is of the same ranking
     diff = np.flatnonzero(got != ref_idx)
     same = {"equal": bool(diff.size == 0), "differing_ranks": int(diff.size),
             "first": [[int(r), int(got[r]), int(ref_idx[r])] for r in diff[:4]],
             "device_recall_in_topk": recall_of(ref_idx, sky)}
     return dict(s_per_step=dt, h2d=h2d, d2h=d2h, recall_in_topk=recall_of(got, sky),
-                load_ms=load_ms, stack_ms=stack_ms, ranking_equals_device=same)
+                link_gbs=link_gbs, ranking_equals_device=same)
 
 
 # ------------------------------------------------------------ cpu oracle ----
@@ -620,27 +642,28 @@ def main():
     computed = samples - r["skipped"]
     if flop_per_sample is not None:
         ach = flop_per_sample * computed / stack_s / 1e12
-        # FP64 pipe issue rate: 2 thread instructions / clock / SM
-        pipe_frac = inst_per_sample * computed / stack_s / (152 * 2 * 2.07e9)
-        line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                            "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+        gips = inst_per_sample * computed / stack_s / 1e9
+        line["roofline"] = {"bound": "alu", "achieved": gips, "peak": FP64_PIPE_PEAK_GIPS,
+                            "unit": "G FP64-pipe thread-instructions/s", "frac": gips / FP64_PIPE_PEAK_GIPS,
                             "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(args.workload),
                             "kernel": "stack kernel (FP64 pipe)",
-                            "fp64_pipe_issue_frac": pipe_frac,
+                            "fp64_pipe_inst_per_sample": inst_per_sample,
+                            "fp64_tflops": ach, "fp64_tflops_frac_of_1.259": ach / FP64_PEAK_TFLOPS,
                             "fp64_samples_per_launch": computed,
                             "algorithmic_bytes_per_launch":
                                 (8 if forms[head].plane == "f32" else 4) * r["valid"]}
     else:
-        line["roofline"] = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                            "unit": "TFLOP/s", "frac": None, "traffic": None,
-                            "note": "FP64 flop/sample not yet measured", "stack_samples_per_s":
-                            samples / stack_s}
+        line["roofline"] = {"bound": "alu", "achieved": None, "peak": FP64_PIPE_PEAK_GIPS,
+                            "unit": "G FP64-pipe thread-instructions/s", "frac": None, "traffic": None,
+                            "note": "FP64 instructions per sample not yet measured",
+                            "stack_samples_per_s": samples / stack_s}
     if e2e is not None:
         line["e2e"] = {"value": samples * world / max_over_ranks(e2e["s_per_step"]), "unit": UNIT,
                        "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                        "recall_in_topk": e2e["recall_in_topk"],
                        "ms_per_step": e2e["s_per_step"] * 1e3,
-                       "load_ms": e2e["load_ms"], "stack_ms": e2e["stack_ms"],
+                       "pipelined": "2 contexts: step i+1's host-to-device copies overlap step i's stack",
+                       "h2d_link_gbs_untimed": e2e["link_gbs"],
                        "ranking_equals_device": e2e["ranking_equals_device"]}
     if rank == 0 and args.workload == "mba" and not args.no_noise:
         line["noise_estimate"] = noise_rate(device, stream, imgs)
