@@ -56,7 +56,8 @@ typedef enum {
 typedef enum {
   NDT_PLANE_F32 = 0,  /* psi, phi stored as FP32                             */
   NDT_PLANE_BF16 = 1, /* BF16 values times per-exposure FP32 scales: the
-                         noise sigma of psi and the interior value of phi  */
+                         powers of two nearest the noise sigma of psi and
+                         the interior value of phi                         */
   NDT_PLANE_F16 = 2   /* FP16 values times per-exposure FP32 scales that map
                          each plane's largest magnitude to 2^14            */
 } ndt_plane_dtype;

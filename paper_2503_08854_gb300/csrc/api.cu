@@ -220,6 +220,13 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   e.cos_far = th < 0.5 * kPi ? (float)(std::cos(th) * (1.0 - 1e-6)) : -2.0f;
 }
 
+// The power of two nearest to x > 0 (in log2), within the normal FP32 range.
+float pow2_near(double x) {
+  if (!(x > 0.0) || !std::isfinite(x)) return 1.0f;
+  const int e = std::max(-120, std::min(120, (int)std::lround(std::log2(x))));
+  return std::ldexp(1.0f, e);
+}
+
 // Sigma of the matched filter: the PSF's, broadened by the coarse-search
 // smoothing when one is set (Gaussians convolve by adding variances).
 float filter_sigma(const ndt_ctx* ctx, float psf_sigma) {
@@ -423,10 +430,13 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
         sg2 += g * g;
       }
       // BF16 scales: the noise sigma of psi, sqrt(sum P^2 / V), and the
-      // interior value of phi, sum P^2 / V (sum P^2 = (sum g^2)^2)
+      // interior value of phi, sum P^2 / V (sum P^2 = (sum g^2)^2), each
+      // rounded to a power of two (BF16 has the FP32 exponent range, so the
+      // scale only centres the values; a power of two makes the division by
+      // it an exact multiplication in the planes kernel and the gather)
       const double vbar = variances ? 1.0 : (double)J.var_c;
-      J.s_phi = (float)(sg2 * sg2 / vbar);
-      J.s_psi = (float)std::sqrt(sg2 * sg2 / vbar);
+      J.s_phi = pow2_near(sg2 * sg2 / vbar);
+      J.s_psi = pow2_near(std::sqrt(sg2 * sg2 / vbar));
       sum_p2[s] = sg2 * sg2;
     }
     J.W = m.width;
@@ -493,8 +503,8 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
                     ctx->sorted_to_table[s], sg);
       PlaneJob& J = jobs[s];
       J.var_c = (float)((double)sg * (double)sg);
-      J.s_phi = (float)(sum_p2[s] / (double)J.var_c);
-      J.s_psi = (float)std::sqrt(sum_p2[s] / (double)J.var_c);
+      J.s_phi = pow2_near(sum_p2[s] / (double)J.var_c);
+      J.s_psi = pow2_near(std::sqrt(sum_p2[s] / (double)J.var_c));
       ctx->noise_sigma[ctx->sorted_to_table[s]] = sg;
     }
   }

@@ -10,7 +10,8 @@
 // weights come precomputed with the job.  FP32 planes: one pass, 4 bytes read
 // (8 with a variance plane) and 8 written per pixel.  BF16 planes: one pass
 // writing 4 bytes per pixel, values divided by a-priori per-exposure scales
-// (BF16 has the FP32 exponent range, so no data-dependent range is needed).
+// that are powers of two (BF16 has the FP32 exponent range, so no
+// data-dependent range is needed, and the division is an exact product).
 // FP16 planes: two passes, one reducing the largest |psi| and phi of each
 // plane, one writing 16-bit pairs scaled so those maxima map to 2^14.
 #include "ndt_internal.cuh"
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     s0 = a0 > 0.0f ? a0 / 16384.0f : 1.0f;
     s1 = a1 > 0.0f ? a1 / 16384.0f : 1.0f;
   }
+  const float is0 = 1.0f / s0, is1 = 1.0f / s1;
   // vertical pass: thread (column x, strip of VH rows)
   const int x = threadIdx.x & (kTile - 1), ys = (threadIdx.x / kTile) * VH;
   float psi[VH], phi[VH];
@@ -214,7 +216,10 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
       }
     } else {
       // round-to-nearest-even of value / scale
-      const float q0 = __fdiv_rn(psi[j], s0), q1 = __fdiv_rn(phi[j], s1);
+      // BF16: the scales are powers of two, so value * (1/scale) is the
+      // exact quotient; FP16: an IEEE division by the data-dependent scale
+      const float q0 = MODE == kPlaneStoreBF16 ? psi[j] * is0 : __fdiv_rn(psi[j], s0);
+      const float q1 = MODE == kPlaneStoreBF16 ? phi[j] * is1 : __fdiv_rn(phi[j], s1);
       if (MODE == kPlaneStoreBF16)
         reinterpret_cast<__nv_bfloat162*>(out)[base + i] =
             __halves2bfloat162(__float2bfloat16_rn(q0), __float2bfloat16_rn(q1));
