@@ -163,11 +163,20 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const St
   walk_finish(w, a, o, active);
 }
 
-__device__ __forceinline__ void team_sync(int team, int team_threads) {
-  if (team_threads == 32) {
+// Barrier of one team.  The barrier ids are immediates (a team index in a
+// register would make the assembler reserve all 16 named barriers per CTA,
+// which caps residency at 4 CTAs per SM); the team index is warp-uniform.
+template <int TEAM>
+__device__ __forceinline__ void team_sync(int team) {
+  static_assert(TEAM == 32 || TEAM == 64 || TEAM == kBlock, "teams of 1, 2 or 4 warps");
+  if constexpr (TEAM == 32) {
     __syncwarp();
+  } else if constexpr (TEAM == kBlock) {
+    asm volatile("bar.sync 1, %0;" ::"n"(TEAM) : "memory");
+  } else if (team == 0) {
+    asm volatile("bar.sync 1, %0;" ::"n"(TEAM) : "memory");
   } else {
-    asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(team_threads) : "memory");
+    asm volatile("bar.sync 2, %0;" ::"n"(TEAM) : "memory");
   }
 }
 
@@ -186,7 +195,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
   const int tl = threadIdx.x % TEAM;
   for (;;) {
     if (tl == 0) item_sh[team] = (long long)atomicAdd(a.queue_head, 1ull);
-    team_sync(team, TEAM);
+    team_sync<TEAM>(team);
     const long long item = item_sh[team];
     if (item >= a.n_items) break;
     const int64_t fq = upper_bound_i64(a.item_off, a.n_fam + 1, item) - 1;
@@ -212,17 +221,17 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
         const int j = __ldg(a.fam_exp_pos + eb + jj);
         dst[i] = __ldg(reinterpret_cast<const double*>(a.ex + j) + wd);
       }
-      team_sync(team, TEAM);
+      team_sync<TEAM>(team);
       // every lane runs the loop: the off-chip vote is warp-wide
       for (int jj = 0; jj < cnt; ++jj) {
         const ExpDev& e = stage[team][jj];
         if (a.offchip_test && warp_skips(w, a.ph, e, active)) continue;
         walk_sample<PT, true>(w, a.ph, e, a.planes);
       }
-      team_sync(team, TEAM);
+      team_sync<TEAM>(team);
     }
     walk_finish(w, a, o, active);
-    team_sync(team, TEAM);   // every thread has read item_sh before it is rewritten
+    team_sync<TEAM>(team);   // every thread has read item_sh before it is rewritten
   }
 }
 
