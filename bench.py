@@ -57,7 +57,7 @@ TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.9326e9, "batched": 3.7989e9}
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", choices=["mba", "batched"], default="mba",
