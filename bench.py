@@ -50,8 +50,8 @@ FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 FP64_PER_SAMPLE = {"mba": (63.3, 39.6), "batched": (84.4, 53.3)}
 # DRAM bytes (read + write) of one full-size persistent stack launch (BF16
 # planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
-# in a one-pass capture: MBA 1.861 GB + 71.6 MB, batched 3.526 GB + 272.9 MB.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.9326e9, "batched": 3.7989e9}
+# in a one-pass capture: MBA 1.857 GB + 71.1 MB, batched 3.528 GB + 273.0 MB.
+TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.9279e9, "batched": 3.8012e9}
 
 
 def parse():
