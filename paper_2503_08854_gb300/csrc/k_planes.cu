@@ -37,7 +37,10 @@ struct PlaneGeom {
   static constexpr int SMEM_FLOATS = 144 + 2 * (E * ES + E * HS);
 };
 
-template <int MODE, int RM>
+// VP: the jobs carry variance planes (the API gives either one per exposure
+// or none), compiled separately so that the constant-variance form issues no
+// variance-plane instruction at all.
+template <int MODE, int RM, bool VP>
 __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict__ jobs,
                                                      void* __restrict__ out,
                                                      unsigned int* __restrict__ absmax2) {
@@ -59,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
   float* hor = in + E * ES;                    // E rows of stride HS : horizontal pass of psi
   float* inw = hor + E * HS;                   // E rows of stride ES : 1 / V (variance plane only)
   float* horw = inw + E * ES;                  // E rows of stride HS
-  const bool vplane = J.var != nullptr;
+  constexpr bool vplane = VP;
   if (threadIdx.x < NT) {
     const int k = (int)threadIdx.x - RM;
     const bool inside = k >= -R && k <= R;
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
       const bool ok = row_in && c < E && xx >= 0 && xx < W;
       const int64_t p = (int64_t)yy * W + xx;
       a[i][j] = ok ? __ldg(J.image + p) : 0.0f;
-      wv[i][j] = (vplane && ok) ? __ldg(J.var + p) : 0.0f;
+      if constexpr (VP) wv[i][j] = ok ? __ldg(J.var + p) : 0.0f;
     }
   }
 #pragma unroll
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     for (int j = 0; j < CPL; ++j) {
       const int c = lane + 32 * j, xx = x0 + c;
       if (r < E && c < E) {
-        if (vplane) {
+        if constexpr (VP) {
           // outside the image a = w = 0 (zero padding of both planes)
           const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
           const float w = ok ? 1.0f / wv[i][j] : 0.0f;
@@ -121,6 +124,14 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     }
     (along_x ? ex : ey)[threadIdx.x % kTile] = s;
   }
+  // the window weights, once per thread, in registers
+  float gr[NT], gr2[VP ? NT : 1];
+#pragma unroll
+  for (int k = 0; k < NT; ++k) gr[k] = gw[k];
+  if constexpr (VP) {
+#pragma unroll
+    for (int k = 0; k < NT; ++k) gr2[k] = gw2[k];
+  }
   // horizontal pass: a thread slides a register window along HW outputs
   for (int item = threadIdx.x; item < E * (kTile / HW); item += kThreads) {
     const int r = item / (kTile / HW), c0 = (item % (kTile / HW)) * HW;
@@ -134,14 +145,14 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
       for (int j = 0; j < HW; ++j) acc[j] = 0.0f;
 #pragma unroll
       for (int k = 0; k < NT; ++k) {
-        const float g = gw[k];
+        const float g = gr[k];
 #pragma unroll
         for (int j = 0; j < HW; ++j) acc[j] = fmaf(g, w[j + k], acc[j]);
       }
 #pragma unroll
       for (int j = 0; j < HW; ++j) hor[r * HS + c0 + j] = acc[j];
     }
-    if (vplane) {
+    if constexpr (VP) {
       float w[HW + 2 * RM];
       const float* row = inw + r * ES + c0;
 #pragma unroll
@@ -151,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
       for (int j = 0; j < HW; ++j) acc[j] = 0.0f;
 #pragma unroll
       for (int k = 0; k < NT; ++k) {
-        const float g = gw2[k];
+        const float g = gr2[k];
 #pragma unroll
         for (int j = 0; j < HW; ++j) acc[j] = fmaf(g, w[j + k], acc[j]);
       }
@@ -182,12 +193,12 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     for (int j = 0; j < VH; ++j) psi[j] = 0.0f;
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      const float g = gw[k];
+      const float g = gr[k];
 #pragma unroll
       for (int j = 0; j < VH; ++j) psi[j] = fmaf(g, v[j + k], psi[j]);
     }
   }
-  if (vplane) {
+  if constexpr (VP) {
     float v[VH + 2 * RM];
 #pragma unroll
     for (int t = 0; t < VH + 2 * RM; ++t) v[t] = horw[(ys + t) * HS + x];
@@ -195,7 +206,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     for (int j = 0; j < VH; ++j) phi[j] = 0.0f;
 #pragma unroll
     for (int k = 0; k < NT; ++k) {
-      const float g = gw2[k];
+      const float g = gr2[k];
 #pragma unroll
       for (int j = 0; j < VH; ++j) phi[j] = fmaf(g, v[j + k], phi[j]);
     }
@@ -264,26 +275,31 @@ __global__ void __launch_bounds__(kThreads) k_plane_decode(const void* __restric
   }
 }
 
-template <int MODE, int RM>
-cudaError_t launch_rm(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, bool any_var, void* out,
+template <int MODE, int RM, bool VP>
+cudaError_t launch_rm(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, void* out,
                       unsigned int* absmax2, cudaStream_t st) {
   using G = PlaneGeom<RM>;
   // the variance-plane half of the buffers is only needed with variance planes
-  const size_t smem = sizeof(float) * (any_var ? G::SMEM_FLOATS : 144 + G::E * G::ES + G::E * G::HS);
-  cudaError_t e = cudaFuncSetAttribute(k_planes<MODE, RM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = sizeof(float) * (VP ? G::SMEM_FLOATS : 144 + G::E * G::ES + G::E * G::HS);
+  cudaError_t e = cudaFuncSetAttribute(k_planes<MODE, RM, VP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float) * G::SMEM_FLOATS));
   if (e != cudaSuccess) return e;
   dim3 grid(max_tiles, n_jobs);
-  k_planes<MODE, RM><<<grid, kThreads, smem, st>>>(jobs_dev, out, absmax2);
+  k_planes<MODE, RM, VP><<<grid, kThreads, smem, st>>>(jobs_dev, out, absmax2);
   return cudaGetLastError();
 }
 
 template <int MODE>
 cudaError_t launch_mode(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
                         void* out, unsigned int* absmax2, cudaStream_t st) {
-  // the window radius of the launch covers the largest one among the jobs
-  if (max_R <= 8) return launch_rm<MODE, 8>(jobs_dev, n_jobs, max_tiles, any_var, out, absmax2, st);
-  return launch_rm<MODE, kMaxPsfRadius>(jobs_dev, n_jobs, max_tiles, any_var, out, absmax2, st);
+  // the window radius of the launch covers the largest one among the jobs;
+  // variance planes come for every exposure or for none
+  if (max_R <= 8) {
+    return any_var ? launch_rm<MODE, 8, true>(jobs_dev, n_jobs, max_tiles, out, absmax2, st)
+                   : launch_rm<MODE, 8, false>(jobs_dev, n_jobs, max_tiles, out, absmax2, st);
+  }
+  return any_var ? launch_rm<MODE, kMaxPsfRadius, true>(jobs_dev, n_jobs, max_tiles, out, absmax2, st)
+                 : launch_rm<MODE, kMaxPsfRadius, false>(jobs_dev, n_jobs, max_tiles, out, absmax2, st);
 }
 
 }  // namespace
