@@ -412,7 +412,7 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     e.s_psi = 1.0f;
     e.s_phi = 1.0f;
     plane_elems += (int64_t)e.tiles_x * tiles_y * kTile * kTile;
-    max_tiles = std::max(max_tiles, e.tiles_x * tiles_y);
+    max_tiles = std::max(max_tiles, planes_ctas_per_job(e.tiles_x, tiles_y));
     PlaneJob& J = jobs[s];
     J.var_c = m.variance > 0.0f ? m.variance : 1.0f;
     J.sigma = filter_sigma(ctx, m.psf_sigma_px);

@@ -4,9 +4,11 @@
 // P the Gaussian of sigma truncated at R = ceil(4 sigma), unit sum over the
 // (2R+1)^2 window, terms outside the image dropped.  The truncated Gaussian
 // factorises, P = g (x) g with g the unit-sum 1-D window, so both planes are
-// separable correlations (zero padding factorises too).  One CTA computes one
-// 32 x 32 output tile from a (32+2R)^2 input tile in shared memory and writes
-// it as one contiguous tile of the tile-major (psi, phi) plane.  The window
+// separable correlations (zero padding factorises too).  One CTA computes a
+// strip of kTY vertically stacked 32 x 32 output tiles from a
+// (32+2R) x (32 kTY+2R) input block in shared memory (taller strips share
+// more of the halo) and writes each as one contiguous tile of the tile-major
+// (psi, phi) plane.  The window
 // weights come precomputed with the job.  FP32 planes: one pass, 4 bytes read
 // (8 with a variance plane) and 8 written per pixel.  BF16 planes: one pass
 // writing 4 bytes per pixel, values divided by a-priori per-exposure scales
@@ -21,6 +23,10 @@ namespace ndt {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef NDT_PLANES_TY
+#define NDT_PLANES_TY 2
+#endif
+constexpr int kTY = NDT_PLANES_TY;   // 32 x 32 tiles per CTA, stacked vertically
 
 // Tile geometry for a compile-time window radius RM >= the jobs' R: the
 // weights are zero-padded to 2 RM + 1 taps, which adds exact zeros in the same
@@ -28,14 +34,20 @@ constexpr int kThreads = 256;
 // every tap loop unroll.
 template <int RM>
 struct PlaneGeom {
-  static constexpr int E = kTile + 2 * RM;   // input tile edge
-  static constexpr int ES = E + 1;           // odd row stride: conflict-free horizontal pass
-  static constexpr int HS = kTile + 1;       // row stride of the horizontal results (odd)
-  static constexpr int NT = 2 * RM + 1;      // taps
-  static constexpr int HW = 8;               // horizontal outputs per thread (sliding window)
-  static constexpr int VH = 4;               // vertical outputs per thread
-  static constexpr int SMEM_FLOATS = 144 + 2 * (E * ES + E * HS);
+  static constexpr int EW = kTile + 2 * RM;        // input block width
+  static constexpr int EH = kTY * kTile + 2 * RM;  // input block height
+  static constexpr int ES = EW + 1;                // odd row stride: conflict-free horizontal pass
+  static constexpr int HS = kTile + 1;             // row stride of the horizontal results (odd)
+  static constexpr int NT = 2 * RM + 1;            // taps
+  static constexpr int HW = 8;                     // horizontal outputs per thread (sliding window)
+  static constexpr int VH = kTY * kTile / (kThreads / kTile);   // vertical outputs per thread
+  static constexpr int HDR = 112 + kTY * kTile;    // weights (2 x 40), ex (32), ey (32 kTY)
+  static constexpr int SMEM_FLOATS = HDR + 2 * (EH * ES + EH * HS);
+  static_assert(kTile % VH == 0, "a thread's vertical outputs lie in one tile");
 };
+
+// CTAs per job: tiles_x x (strips of kTY tile rows)
+int planes_ctas_per_job_impl(int tiles_x, int tiles_y) { return tiles_x * ((tiles_y + kTY - 1) / kTY); }
 
 // VP: the jobs carry variance planes (the API gives either one per exposure
 // or none), compiled separately so that the constant-variance form issues no
@@ -45,23 +57,23 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
                                                      void* __restrict__ out,
                                                      unsigned int* __restrict__ absmax2) {
   using G = PlaneGeom<RM>;
-  constexpr int E = G::E, ES = G::ES, HS = G::HS, NT = G::NT, HW = G::HW, VH = G::VH;
-  static_assert(kThreads == kTile * (kTile / VH), "vertical pass: one thread per (column, strip)");
+  constexpr int EW = G::EW, EH = G::EH, ES = G::ES, HS = G::HS, NT = G::NT, HW = G::HW, VH = G::VH;
+  static_assert((kThreads / kTile) * VH == kTY * kTile, "vertical pass: one thread per (column, strip)");
   const PlaneJob& J = jobs[blockIdx.y];
-  const int tile = blockIdx.x;
-  const int tiles_x = J.tiles_x, W = J.W, H = J.H;
-  if (tile >= tiles_x * J.tiles_y) return;
-  const int tx = tile % tiles_x, ty = tile / tiles_x;
+  const int tiles_x = J.tiles_x, tiles_y = J.tiles_y, W = J.W, H = J.H;
+  const int blk = blockIdx.x;
+  if (blk >= tiles_x * ((tiles_y + kTY - 1) / kTY)) return;
+  const int tx = blk % tiles_x, ty0 = (blk / tiles_x) * kTY;   // first tile row of the strip
   const int R = J.R;
   extern __shared__ float sm[];
   float* gw = sm;                              // NT (<= 33) zero-padded weights
   float* gw2 = sm + 40;
   float* ex = sm + 80;                         // 32: sum of g^2 inside the image along x
-  float* ey = sm + 112;                        // 32: same along y
-  float* in = sm + 144;                        // E rows of stride ES : I / V
-  float* hor = in + E * ES;                    // E rows of stride HS : horizontal pass of psi
-  float* inw = hor + E * HS;                   // E rows of stride ES : 1 / V (variance plane only)
-  float* horw = inw + E * ES;                  // E rows of stride HS
+  float* ey = sm + 112;                        // 32 kTY: same along y
+  float* in = sm + G::HDR;                     // EH rows of stride ES : I / V
+  float* hor = in + EH * ES;                   // EH rows of stride HS : horizontal pass of psi
+  float* inw = hor + EH * HS;                  // EH rows of stride ES : 1 / V (variance plane only)
+  float* horw = inw + EH * ES;                 // EH rows of stride HS
   constexpr bool vplane = VP;
   if (threadIdx.x < NT) {
     const int k = (int)threadIdx.x - RM;
@@ -69,23 +81,23 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     gw[threadIdx.x] = inside ? J.g[k + R] : 0.0f;
     gw2[threadIdx.x] = inside ? J.g2[k + R] : 0.0f;
   }
-  const int x0 = tx * kTile - RM, y0 = ty * kTile - RM;
+  const int x0 = tx * kTile - RM, y0 = ty0 * kTile - RM;
   const float inv_vc = 1.0f / J.var_c;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // input tile: rows by warps, columns by lanes, with compile-time trip
   // counts so that every load of a thread is issued before the first is used
   // (a CTA lives a few microseconds: its loads must overlap, not queue)
   constexpr int kWarps = kThreads / 32;
-  constexpr int RPW = (E + kWarps - 1) / kWarps, CPL = (E + 31) / 32;
+  constexpr int RPW = (EH + kWarps - 1) / kWarps, CPL = (EW + 31) / 32;
   float a[RPW][CPL], wv[RPW][CPL];
 #pragma unroll
   for (int i = 0; i < RPW; ++i) {
     const int r = warp + kWarps * i, yy = y0 + r;
-    const bool row_in = r < E && yy >= 0 && yy < H;
+    const bool row_in = r < EH && yy >= 0 && yy < H;
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
       const int c = lane + 32 * j, xx = x0 + c;
-      const bool ok = row_in && c < E && xx >= 0 && xx < W;
+      const bool ok = row_in && c < EW && xx >= 0 && xx < W;
       const int64_t p = (int64_t)yy * W + xx;
       a[i][j] = ok ? __ldg(J.image + p) : 0.0f;
       if constexpr (VP) wv[i][j] = ok ? __ldg(J.var + p) : 0.0f;
@@ -97,7 +109,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
 #pragma unroll
     for (int j = 0; j < CPL; ++j) {
       const int c = lane + 32 * j, xx = x0 + c;
-      if (r < E && c < E) {
+      if (r < EH && c < EW) {
         if constexpr (VP) {
           // outside the image a = w = 0 (zero padding of both planes)
           const bool ok = yy >= 0 && yy < H && xx >= 0 && xx < W;
@@ -111,18 +123,19 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     }
   }
   __syncthreads();
-  if (!vplane && threadIdx.x < 2 * kTile) {
+  if (!vplane && threadIdx.x < (1 + kTY) * kTile) {
     // constant variance: phi = (1/V) * (sum of g^2 inside the image along x)
     //                                * (sum of g^2 inside the image along y)
     const bool along_x = threadIdx.x < kTile;
-    const int c = (along_x ? tx : ty) * kTile + (threadIdx.x % kTile);
+    const int idx = along_x ? (int)threadIdx.x : (int)threadIdx.x - kTile;
+    const int c = (along_x ? tx : ty0) * kTile + idx;
     const int lim = along_x ? W : H;
     float s = 0.0f;
     for (int k = 0; k < NT; ++k) {
       const int q = c + k - RM;
       if (q >= 0 && q < lim) s += gw2[k];
     }
-    (along_x ? ex : ey)[threadIdx.x % kTile] = s;
+    (along_x ? ex : ey)[idx] = s;
   }
   // the window weights, once per thread, in registers
   float gr[NT], gr2[VP ? NT : 1];
@@ -133,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
     for (int k = 0; k < NT; ++k) gr2[k] = gw2[k];
   }
   // horizontal pass: a thread slides a register window along HW outputs
-  for (int item = threadIdx.x; item < E * (kTile / HW); item += kThreads) {
+  for (int item = threadIdx.x; item < EH * (kTile / HW); item += kThreads) {
     const int r = item / (kTile / HW), c0 = (item % (kTile / HW)) * HW;
     {
       float w[HW + 2 * RM];
@@ -214,10 +227,15 @@ __global__ void __launch_bounds__(kThreads) k_planes(const PlaneJob* __restrict_
 #pragma unroll
     for (int j = 0; j < VH; ++j) phi[j] = ex[x] * ey[ys + j] * inv_vc;
   }
-  const int64_t base = J.plane_off + ((int64_t)tile << (2 * kTileShift));
+  // the thread's rows lie in one tile of the strip; a strip may run past the
+  // last tile row of the image, whose tiles are not stored
+  const int ty = ty0 + ys / kTile, y_in = ys % kTile;
+  const bool tile_ok = ty < tiles_y;
+  const int64_t base = J.plane_off + ((int64_t)(ty * tiles_x + tx) << (2 * kTileShift));
 #pragma unroll
   for (int j = 0; j < VH; ++j) {
-    const int y = ys + j, i = (y << kTileShift) + x;
+    const int y = y_in + j, i = (y << kTileShift) + x;
+    if (!tile_ok) break;
     if (MODE == kPlaneStoreF32) {
       reinterpret_cast<float2*>(out)[base + i] = make_float2(psi[j], phi[j]);
     } else if (MODE == kPlaneAbsMax) {
@@ -276,45 +294,47 @@ __global__ void __launch_bounds__(kThreads) k_plane_decode(const void* __restric
 }
 
 template <int MODE, int RM, bool VP>
-cudaError_t launch_rm(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, void* out,
+cudaError_t launch_rm(const PlaneJob* jobs_dev, int n_jobs, int max_ctas, void* out,
                       unsigned int* absmax2, cudaStream_t st) {
   using G = PlaneGeom<RM>;
   // the variance-plane half of the buffers is only needed with variance planes
-  const size_t smem = sizeof(float) * (VP ? G::SMEM_FLOATS : 144 + G::E * G::ES + G::E * G::HS);
+  const size_t smem = sizeof(float) * (VP ? G::SMEM_FLOATS : G::HDR + G::EH * G::ES + G::EH * G::HS);
   cudaError_t e = cudaFuncSetAttribute(k_planes<MODE, RM, VP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(float) * G::SMEM_FLOATS));
   if (e != cudaSuccess) return e;
-  dim3 grid(max_tiles, n_jobs);
+  dim3 grid(max_ctas, n_jobs);
   k_planes<MODE, RM, VP><<<grid, kThreads, smem, st>>>(jobs_dev, out, absmax2);
   return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_mode(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
+cudaError_t launch_mode(const PlaneJob* jobs_dev, int n_jobs, int max_ctas, int max_R, bool any_var,
                         void* out, unsigned int* absmax2, cudaStream_t st) {
   // the window radius of the launch covers the largest one among the jobs;
   // variance planes come for every exposure or for none
   if (max_R <= 8) {
-    return any_var ? launch_rm<MODE, 8, true>(jobs_dev, n_jobs, max_tiles, out, absmax2, st)
-                   : launch_rm<MODE, 8, false>(jobs_dev, n_jobs, max_tiles, out, absmax2, st);
+    return any_var ? launch_rm<MODE, 8, true>(jobs_dev, n_jobs, max_ctas, out, absmax2, st)
+                   : launch_rm<MODE, 8, false>(jobs_dev, n_jobs, max_ctas, out, absmax2, st);
   }
-  return any_var ? launch_rm<MODE, kMaxPsfRadius, true>(jobs_dev, n_jobs, max_tiles, out, absmax2, st)
-                 : launch_rm<MODE, kMaxPsfRadius, false>(jobs_dev, n_jobs, max_tiles, out, absmax2, st);
+  return any_var ? launch_rm<MODE, kMaxPsfRadius, true>(jobs_dev, n_jobs, max_ctas, out, absmax2, st)
+                 : launch_rm<MODE, kMaxPsfRadius, false>(jobs_dev, n_jobs, max_ctas, out, absmax2, st);
 }
 
 }  // namespace
 
-cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
+int planes_ctas_per_job(int tiles_x, int tiles_y) { return planes_ctas_per_job_impl(tiles_x, tiles_y); }
+
+cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_ctas, int max_R, bool any_var,
                           int mode, void* out, unsigned int* absmax2, cudaStream_t st) {
   switch (mode) {
     case kPlaneStoreF32:
-      return launch_mode<kPlaneStoreF32>(jobs_dev, n_jobs, max_tiles, max_R, any_var, out, absmax2, st);
+      return launch_mode<kPlaneStoreF32>(jobs_dev, n_jobs, max_ctas, max_R, any_var, out, absmax2, st);
     case kPlaneAbsMax:
-      return launch_mode<kPlaneAbsMax>(jobs_dev, n_jobs, max_tiles, max_R, any_var, out, absmax2, st);
+      return launch_mode<kPlaneAbsMax>(jobs_dev, n_jobs, max_ctas, max_R, any_var, out, absmax2, st);
     case kPlaneStoreBF16:
-      return launch_mode<kPlaneStoreBF16>(jobs_dev, n_jobs, max_tiles, max_R, any_var, out, absmax2, st);
+      return launch_mode<kPlaneStoreBF16>(jobs_dev, n_jobs, max_ctas, max_R, any_var, out, absmax2, st);
     case kPlaneStoreF16:
-      return launch_mode<kPlaneStoreF16>(jobs_dev, n_jobs, max_tiles, max_R, any_var, out, absmax2, st);
+      return launch_mode<kPlaneStoreF16>(jobs_dev, n_jobs, max_ctas, max_R, any_var, out, absmax2, st);
   }
   return cudaErrorInvalidValue;
 }

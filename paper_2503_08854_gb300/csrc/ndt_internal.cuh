@@ -625,7 +625,10 @@ struct PlaneJob {
 // of each plane, then BF16/FP16 pairs scaled by those maxima.
 enum PlaneMode : int32_t { kPlaneStoreF32 = 0, kPlaneAbsMax = 1, kPlaneStoreBF16 = 2, kPlaneStoreF16 = 3 };
 
-cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_tiles, int max_R, bool any_var,
+// CTAs of the planes kernel per exposure of tiles_x x tiles_y tiles; a launch
+// takes the largest over its exposures as grid.x ("max_ctas" below).
+int planes_ctas_per_job(int tiles_x, int tiles_y);
+cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_ctas, int max_R, bool any_var,
                           int mode, void* out, unsigned int* absmax2, cudaStream_t st);
 cudaError_t launch_plane_decode(const void* planes, int plane_type, const ExpDev* e_host_copy,
                                 float* psi, float* phi, cudaStream_t st);
