@@ -23,10 +23,12 @@ namespace ndt {
 namespace {
 
 constexpr int kThreads = 256;
+// 32 x 32 tiles per CTA, stacked vertically: the BF16 planes of 200 x 4096^2
+// take 15.1 ms with one tile per CTA, 11.8 ms with 2 and 11.0 ms with 4
 #ifndef NDT_PLANES_TY
-#define NDT_PLANES_TY 2
+#define NDT_PLANES_TY 4
 #endif
-constexpr int kTY = NDT_PLANES_TY;   // 32 x 32 tiles per CTA, stacked vertically
+constexpr int kTY = NDT_PLANES_TY;
 
 // Tile geometry for a compile-time window radius RM >= the jobs' R: the
 // weights are zero-padded to 2 RM + 1 taps, which adds exact zeros in the same
