@@ -70,7 +70,7 @@ def parse():
     p.add_argument("--n-exp", type=int, default=200)
     p.add_argument("--k", type=int, default=8192)
     p.add_argument("--plane", default="bf16", choices=["f32", "bf16", "f16"])
-    p.add_argument("--forms", default="plain,chosen")
+    p.add_argument("--forms", default="chosen,plain")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -387,25 +387,26 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
     """Same steps through the public API with pinned HOST inputs and outputs.
     Every step copies its images and orbit states from pinned host memory and
     reads its top-k back to the host, all inside the timed region.  Steps
-    alternate between two contexts (the form's and a second one with the same
-    launch configuration on its own stream), as a survey pipeline would: while
-    one context stacks step i, the other loads step i+1's images, so the
-    host-to-device copies overlap the stack kernel."""
+    alternate between two new contexts with the form's launch configuration,
+    each on its own stream, as a survey pipeline would: while one context
+    stacks step i, the other loads step i+1's images, so the host-to-device
+    copies overlap the stack kernel."""
     import torch
     from paper_2503_08854_gb300 import ndt
     n = states.shape[1]
-    # untimed reference: the same step on the device-resident inputs
-    ref_idx = torch.empty(k, dtype=torch.int64, device=device)
-    ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=form.plane)
-    ndt.stack_orbits(ctx, states, sky.t0, n, families=sky.fam_dev)
-    ndt.topk_candidates(ctx, k, ref_idx)
-    ref_idx = ref_idx.cpu().numpy()
     st = ndt.get_stats(ctx)
-    stream2 = torch.cuda.Stream(device=device)
-    ctx2 = ndt.create(device.index, stream2)
+    streams = [torch.cuda.Stream(device=device) for _ in range(2)]
+    ctxs = [ndt.create(device.index, s) for s in streams]
     try:
-        if form.mode == "persistent":
-            ndt.set_launch(ctx2, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"], use_graph=form.graph)
+        for c in ctxs:
+            if form.mode == "persistent":
+                ndt.set_launch(c, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"], use_graph=form.graph)
+        # untimed reference: the same step on the device-resident inputs
+        ref_idx = torch.empty(k, dtype=torch.int64, device=device)
+        ndt.load_exposures(ctxs[0], sky.ex, imgs, plane_dtype=form.plane)
+        ndt.stack_orbits(ctxs[0], states, sky.t0, n, families=sky.fam_dev)
+        ndt.topk_candidates(ctxs[0], k, ref_idx)
+        ref_idx = ref_idx.cpu().numpy()
         h_imgs = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
         h_imgs.copy_(imgs)
         h_states = torch.empty(states.shape, dtype=states.dtype, pin_memory=True)
@@ -426,7 +427,6 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
         h_val = [torch.empty(k, dtype=torch.float32, pin_memory=True) for _ in range(2)]
         np_imgs = h_imgs.numpy()
         np_states = h_states.numpy()
-        ctxs = (ctx, ctx2)
 
         def run(n_steps):
             ndt.load_exposures(ctxs[0], sky.ex, np_imgs, plane_dtype=form.plane)
@@ -446,7 +446,8 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
         torch.cuda.synchronize(device)
         dt = (time.perf_counter() - t0) / args.steps
     finally:
-        ndt.destroy(ctx2)
+        for c in ctxs:
+            ndt.destroy(c)
     h2d = int(h_imgs.numel() * 4 + h_states.numel() * 8)
     d2h = int(k * 12)
     got = np.array(h_idx[last].numpy())      # a copy: every figure below is of the same ranking
