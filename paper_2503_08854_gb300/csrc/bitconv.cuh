@@ -5,7 +5,7 @@
 // helpers do the same conversions with integer and logic instructions, which
 // run on other pipes with plenty of spare issue slots.  They compile for the
 // host too (plain C++), so that they can be checked there against the
-// hardware conversions and std::floor.
+// hardware conversions.
 #pragma once
 
 #include <climits>
@@ -102,22 +102,6 @@ NDT_HD double f2d_exact(float f) {
   const unsigned hi = sign | (eh << 20) | (e == 0u ? 0u : m >> 3);
   const unsigned lo = e == 0u ? 0u : m << 29;
   return from_words(hi, lo);
-}
-
-// floor(v) as an int, exactly (no rounding is involved): |v| = m 2^-s with m
-// the 53-bit significand, so floor|v| = m >> s, and a negative v with a
-// fractional part goes one further down.  |v| >= 2^30, infinities and NaN
-// give INT_MIN.
-NDT_HD int floor_to_int(double v) {
-  const unsigned hi = hi_word(v), lo = lo_word(v);
-  const int ex = (int)((hi >> 20) & 0x7FFu);
-  const int s = 1075 - ex;                      // shift that takes m to the integer part
-  if (s < 23) return INT_MIN;                   // |v| >= 2^30
-  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | (ex != 0 ? 0x100000u : 0u)) << 32) | lo;
-  const int sh = s < 63 ? s : 63;               // |v| < 2^-11: integer part 0
-  const int q = (int)(m >> sh);
-  const int frac = (m << (64 - sh)) != 0ull ? 1 : 0;
-  return (hi & 0x80000000u) ? -q - frac : q;
 }
 
 }  // namespace ndt

@@ -510,15 +510,6 @@ __device__ __forceinline__ bool project_h(const ExpDev& e, const double rho[3], 
   return true;
 }
 
-// Nearest pixel (pixel i spans [i - 1/2, i + 1/2)) from the shifted
-// coordinates of project_h; false outside the image.  The floor runs on the
-// integer pipe; coordinates beyond 2^30 give INT_MIN, outside every image.
-__device__ __forceinline__ bool nearest_pixel(const ExpDev& e, double xh, double yh, int& ix, int& iy) {
-  ix = floor_to_int(xh);
-  iy = floor_to_int(yh);
-  return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;
-}
-
 // Nearest pixel of a topocentric vector (double-float, from apparent_rho_df)
 // through the TAN projection in double-float arithmetic (~48-bit dot
 // products and quotient): the same x + 1/2 and

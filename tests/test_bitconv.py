@@ -2,10 +2,9 @@
 from the same headers as the kernel:
 
 * the integer-pipe conversions (FP64 -> FP32 truncated and rounded, FP32 ->
-  FP64, floor to int) against the host's conversions and std::floor on
-  special values, every neighbour of the integers and half-integers of the
-  image range, FP32 rounding ties and random bit patterns
-  (tests/native/check_bitconv.cpp);
+  FP64) against the host's conversions on special values, every neighbour
+  of the integers and half-integers of the image range, FP32 rounding ties
+  and random bit patterns (tests/native/check_bitconv.cpp);
 * the double-float helpers of the TAN projection (FP64 split, dot product,
   quotient, floor) against long double, and the whole projection at 0.2
   arcsec pixels to 5e-8 px (tests/native/check_dfloat.cpp)."""
