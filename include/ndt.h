@@ -10,7 +10,7 @@
  * and the observer position, projects through the exposure's tangent-plane
  * WCS (sec. 3), gathers matched-filter planes psi, phi at the nearest pixel
  * (sec. 3, Gaussian-PSF matched filter) and accumulates the constant-flux
- * stacked statistic (sec. 3, "same flux in each image"), then ranks orbits
+ * stacked statistic (sec. 3, constant flux across images), then ranks orbits
  * (Algorithm 1, FindSignificantResults).
  *
  * Conventions shared by every entry point
@@ -124,8 +124,8 @@ ndt_status ndt_set_constants(ndt_ctx *ctx, double gm, double c_light, double obl
 
 /*
  * load_exposures: store the exposure table and compute the matched-filter
- * planes of every image (paper sec. 3: matched filter with a Gaussian PSF
- * whose width is given in the image header):
+ * planes of every image (paper sec. 3: a matched filter for a Gaussian PSF,
+ * its width read from each image's header):
  *   psi_j(p) = sum_k P_j(k) I_j(p+k) / V_j(p+k),
  *   phi_j(p) = sum_k P_j(k)^2 / V_j(p+k),
  * P_j the Gaussian of sigma_j truncated at R = ceil(4 sigma_j) and
@@ -148,8 +148,8 @@ ndt_status ndt_load_exposures(ndt_ctx *ctx, const ndt_exposure *meta, int32_t n_
  * propagate o to the epoch of j (two-body, paper sec. 3), correct for light
  * time, project through the WCS of j, and if the nearest pixel
  * (floor(x + 1/2), floor(y + 1/2)) lies inside the image add psi_j, phi_j
- * there to the orbit's sums (paper sec. 3, filter to image boundaries and
- * combine assuming constant flux):
+ * there to the orbit's sums (paper sec. 3: intersections outside the image
+ * are discarded and the rest combined under a constant-flux assumption):
  *   Psi_o = sum psi,  Phi_o = sum phi,  n_o = number of valid samples,
  *   nu_o  = Psi_o / sqrt(Phi_o) if Phi_o > 0 and n_o >= min_obs, else -inf.
  * Families (CSR): family f owns orbits [fam_orbit_off[f], fam_orbit_off[f+1])
@@ -237,8 +237,8 @@ ndt_status ndt_autotune(ndt_ctx *ctx, const double *states, double t0, int64_t n
                         const int32_t *fam_exp_idx, int32_t n_fam, float *times_ms);
 
 /*
- * Learned vetting (paper sec. 5.2.3: a neural network that recognises
- * prepared image stacks of true and false positives, left there as future
+ * Learned vetting (paper sec. 5.2.3: a network that learns to tell stacked
+ * images of real detections from stacks of false ones, left there as future
  * work; the stamp and the network below are this library's reading).
  *
  * stamps: for each candidate (an index into the orbit batch `states`, SoA
@@ -284,8 +284,8 @@ ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, flo
 
 /*
  * noise_mad: per-image noise by the iterative median absolute deviation
- * (paper sec. 3: pixel noise variance from an iterative version of the MAD
- * on each image's pixels).  For image i (n_pixels[i] FP32 values at
+ * (paper sec. 3: each image's pixel noise variance comes from an iterated
+ * MAD of its pixels).  For image i (n_pixels[i] FP32 values at
  * images[i], host or device memory), with S_0 = every pixel:
  *   m = lower median of S (the element of rank floor((n-1)/2)),
  *   sigma = fl32(1.4826 * lower median of fl32|x - m| over S),
@@ -303,8 +303,8 @@ ndt_status ndt_noise_mad(ndt_ctx *ctx, const float *const *images, const int64_t
 
 /*
  * trim_candidates: outlier trimming of candidates' intersections (paper
- * sec. 5.2.3 removes intersections whose SNR is anomalously high compared
- * with the expectation, by sigma clipping, and recomputes the stacked SNR).
+ * sec. 5.2.3 drops intersections whose SNR lies far above what the
+ * candidate predicts, by sigma clipping, and recomputes the stacked SNR).
  * For each candidate cand_idx[i] (an index into the orbit batch `states`, SoA
  * 6 x n_orbits as in stack_orbits, host or device), its valid intersections
  * j (nearest pixel inside the image, phi_j > 0) are clipped by the rule

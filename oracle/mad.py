@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-The paper (sec. 3) computes each image's pixel noise variance with an
-iterative version of the median absolute deviation and states no more.  The
+The paper (sec. 3) derives each image's pixel noise variance from a median
+absolute deviation that is iterated, and gives no further detail.  The
 reading built to here, per image of FP32 pixels x:
 
     S_0 = every pixel

@@ -19,7 +19,7 @@
  *        exposure's tangent point and inverse CD matrix to pixels (sec. 3,
  *        World Coordinate System projection, Calabretta & Greisen 2002);
  *     4. keep the sample only if the nearest pixel lies inside the image
- *        (sec. 3, filter to image boundaries);
+ *        (sec. 3: intersections outside the image are discarded);
  *     5. matched filter with a Gaussian PSF (sec. 3): psi = sum P*I/V and
  *        phi = sum P^2/V over the truncated PSF window at that pixel;
  *     6. constant-flux combination (sec. 3): Psi = sum psi, Phi = sum phi,

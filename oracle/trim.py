@@ -3,10 +3,9 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper (sec. 5.2.3, the outlier figure there) removes false positives
-caused by an artefact in a single difference image: intersections whose
-individual SNR is anomalously high compared with what the constant-flux
-combination of the others expects are dropped, by simple sigma clipping,
-and the stacked SNR recomputed.  It fixes neither the statistic nor the
+caused by an artefact in a single difference image: an intersection whose
+own SNR lies far above what the constant-flux combination of the others
+predicts is dropped (sigma clipping) and the stacked SNR is recomputed.  It fixes neither the statistic nor the
 threshold; the readings built to here:
 
 For candidate orbit o, the valid intersections j (nearest pixel inside the

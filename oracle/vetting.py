@@ -3,8 +3,9 @@ candidate's track and a small CNN that scores them.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-The paper names this stage as future work (sec. 5.2.3: a neural network
-trained to recognise prepared image stacks of true and false positives) and
+The paper names this stage as future work (sec. 5.2.3: a network
+that learns to tell stacked images of real detections from stacks of false
+ones) and
 fixes neither the stamp nor the network.  The definitions here are the
 readings this project builds to:
 

@@ -698,7 +698,10 @@ ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
       NDT_CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "capture begin");
       cudaError_t e = enqueue();
       cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "captured stack");
+      if (e != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(g);
+        return cuda_fail(ctx, e, "captured stack");
+      }
       NDT_CK(e2, "capture end");
       NDT_CK(cudaGraphInstantiate(&ctx->graph, g, 0), "graph instantiate");
       cudaGraphDestroy(g);
@@ -732,7 +735,9 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   if (n_orbits > 0 && !states) return fail(ctx, NDT_EINVAL, "states is null");
   if (n_fam < 0) return fail(ctx, NDT_EINVAL, "n_fam < 0");
   if (!std::isfinite(t0)) return fail(ctx, NDT_EINVAL, "t0 not finite");
-  StackArgs a{};
+  // zeroed bytes, padding included: the graph-reuse key compares the raw bytes
+  StackArgs a;
+  std::memset(&a, 0, sizeof a);
   const bool persistent = ctx->mode == NDT_LAUNCH_PERSISTENT;
   ndt_status s = prepare_families(ctx, n_orbits, fam_orbit_off, fam_exp_off, fam_exp_idx, n_fam,
                                   persistent, ctx->orbit_tile, a);

@@ -1,6 +1,6 @@
 // k_mad.cu -- per-image noise estimate by the iterative median absolute
-// deviation (paper sec. 3: pixel noise variance from an iterative version of
-// the MAD on each image's pixels).
+// deviation (paper sec. 3: each image's pixel noise variance comes from an
+// iterated MAD of its pixels).
 //
 // Rule, per image of FP32 pixels x (S_0 = every pixel):
 //   m_i = lower median of S_i (rank floor((n-1)/2)),

@@ -1,5 +1,5 @@
-// k_planes.cu -- matched-filter planes (paper sec. 3: matched filter with a
-// Gaussian PSF whose width is given in the image header):
+// k_planes.cu -- matched-filter planes (paper sec. 3: a matched filter for
+// a Gaussian PSF, its width read from each image's header):
 //   psi(p) = sum_k P(k) I(p+k) / V(p+k),   phi(p) = sum_k P(k)^2 / V(p+k),
 // P the Gaussian of sigma truncated at R = ceil(4 sigma), unit sum over the
 // (2R+1)^2 window, terms outside the image dropped.  The truncated Gaussian

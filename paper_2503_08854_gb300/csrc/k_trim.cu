@@ -1,7 +1,7 @@
 // k_trim.cu -- outlier trimming of candidates' intersections (paper
-// sec. 5.2.3: intersections whose own SNR is anomalously high for the
-// constant-flux combination of the others are removed by sigma clipping and
-// the stacked SNR recomputed).
+// sec. 5.2.3: an intersection whose own SNR lies far above what the
+// constant-flux combination of the others predicts is dropped by sigma
+// clipping, and the stacked SNR is recomputed).
 //
 // Rule (the paper fixes neither statistic nor threshold).  For a candidate's
 // valid intersections j (nearest pixel inside the image, phi_j > 0), with

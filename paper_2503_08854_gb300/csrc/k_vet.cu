@@ -1,6 +1,6 @@
-// k_vet.cu -- learned vetting of candidates (paper sec. 5.2.3: a neural
-// network trained to recognise prepared image stacks of true and false
-// positives; the paper leaves it as future work and fixes no architecture).
+// k_vet.cu -- learned vetting of candidates (paper sec. 5.2.3: a network
+// that learns to tell stacked images of real detections from stacks of false
+// ones; the paper leaves it as future work and fixes no architecture).
 //
 // Stamps.  For each candidate the positions along its track are computed by
 // the same device code as the stacking path; one CTA then accumulates, for

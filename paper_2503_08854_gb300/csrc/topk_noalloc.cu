@@ -36,6 +36,7 @@ void* g_addr[kMaxDevices] = {};
 
 // Device address of g_topk_scratch on `device` (looked up once per device).
 cudaError_t scratch_address(int device, void** out) {
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[device]) {
     int prev = -1;
@@ -75,6 +76,7 @@ extern "C" ndt_status ndt_topk_noalloc(const float* snr_dev, int64_t n, int64_t 
   if (k < 1 || k > kNoallocMaxK) return NDT_EINVAL;
   int dev = -1, d2 = -1;
   if (!on_device(snr_dev, &dev)) return NDT_EINVAL;
+  if (dev < 0 || dev >= kMaxDevices) return NDT_EINVAL;   // beyond the address cache
   if (idx_out && (!on_device(idx_out, &d2) || d2 != dev)) return NDT_EINVAL;
   if (snr_out && (!on_device(snr_out, &d2) || d2 != dev)) return NDT_EINVAL;
   void* scratch = nullptr;

@@ -1,5 +1,5 @@
-"""Learned vetting of stacked candidates (paper sec. 5.2.3: a neural network
-that recognises prepared image stacks of true and false positives).
+"""Learned vetting of stacked candidates (paper sec. 5.2.3: a network that
+learns to tell stacked images of real detections from stacks of false ones).
 
 Training runs on the GPU through the library's own kernels: ndt_cnn_loss_grad
 (forward + backward of the 52,929-parameter CNN) and ndt_cnn_adam_step.  The

@@ -1,6 +1,6 @@
 """Pins of the oracle's matched filter, constant-flux stacking and ranking
-(paper sec. 3: matched filter with a Gaussian PSF whose width comes from the
-header, signal combined assuming the same flux in every image; Algorithm 1,
+(paper sec. 3: a matched filter for a Gaussian PSF of the header's width,
+per-image signals combined under a constant-flux assumption; Algorithm 1,
 FindSignificantResults)."""
 import math
 
