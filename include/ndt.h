@@ -262,9 +262,11 @@ ndt_status ndt_stamps(ndt_ctx *ctx, const double *states, double t0, int64_t n_o
    linear 32->1 giving a logit. */
 int64_t ndt_cnn_param_count(void);
 
-/* Logits of n BF16 stamps [n][2][21][21] on the tensor core: layers 2 and 3
-   take BF16 weights and BF16 activations with FP32 accumulation (layer 1 is
-   FP32).  NDT_ETIMEOUT if a bounded device wait gave up (logits then NaN). */
+/* Logits of n BF16 stamps [n][2][21][21] on the tensor core: all three
+   layers take BF16 weights (rounded from the FP32 params, RNE), layers 2 and
+   3 BF16 activations, with FP32 accumulation; bias, pooling and the linear
+   head are FP32.  NDT_ETIMEOUT if a bounded device wait gave up (logits then
+   NaN). */
 ndt_status ndt_cnn_forward(ndt_ctx *ctx, const float *params, const uint16_t *stamps_bf16,
                            int64_t n, float *logits);
 

@@ -208,3 +208,101 @@ def loss_and_grad(theta, x, y):
     dy1 = da1 * (c["y1"] > 0)
     _, grads["w1"], grads["b1"] = _conv_backward(c["x"], p["w1"], dy1)
     return loss, pack(grads)
+
+
+# ------------------------------------------- error bound of BF16 scoring --
+#
+# A scorer that rounds the network's convolution operands to BF16 (unit
+# roundoff u = 2^-8 for round-to-nearest-even) and accumulates in FP32
+# computes a logit z~ that differs from the exact logit z of forward().  The
+# bound below takes that difference in two parts.
+#
+# BF16 operand rounding.  Every rounded operand v (a weight of w1, w2 or w3,
+# an activation of a1 or a2; the stamps are BF16 already) becomes v (1 + d)
+# with |d| <= u.  To first order the logit moves by sum_i c_i d_i with
+# c_i = (dz/dv_i) v_i, the operand's sensitivity times its value, both from
+# the exact network.  Under the probabilistic model of rounding (Higham &
+# Mary 2019: the d_i independent, mean zero, |d_i| <= u), Hoeffding's
+# inequality gives P(|sum c_i d_i| >= lam u sqrt(sum c_i^2)) <=
+# 2 exp(-lam^2 / 2), 4.6e-11 at lam = 7.
+#
+# FP32 accumulation.  Each output of layer l (K_l = 25 C_in products plus
+# the bias) and the pooling (441 terms) and head (33 terms) sums are
+# bounded in the worst case, whatever the summation order or rounding mode,
+# by 2 n u32 sum_k |term_k| (u32 = 2^-24; the factor 2 admits truncating
+# adders), carried to the logit by |dz/dy|.
+#
+# The bound neglects second-order terms (relative size ~u) and the few
+# activations whose sign a perturbation flips (a ReLU kink moves such an
+# element by at most its own perturbation).
+
+U_BF16 = 2.0 ** -8
+U_FP32 = 2.0 ** -24
+
+
+def _conv_abs(x, w):
+    """|w| correlated with |x| (zero padding), no bias: the sum of the term
+    magnitudes under each output."""
+    return conv2d(np.abs(x), np.abs(w), np.zeros(w.shape[0]))
+
+
+def _conv_backward_per_stamp(x, w, dy):
+    """Per-stamp gradients of conv2d: dx (B,C,H,W) and dw (B,O,C,K,K)."""
+    B, C, H, W = x.shape
+    O, _, KK, _ = w.shape
+    p = KK // 2
+    cols = _cols(x, KK)                                        # (B, C*KK*KK, HW)
+    dyf = dy.reshape(B, O, H * W)
+    dw = np.matmul(dyf, cols.transpose(0, 2, 1)).reshape((B,) + w.shape)
+    dcols = np.matmul(w.reshape(O, -1).T, dyf).reshape(B, C, KK, KK, H, W)
+    dxp = np.zeros((B, C, H + 2 * p, W + 2 * p))
+    for u in range(KK):
+        for v in range(KK):
+            dxp[:, :, u:u + H, v:v + W] += dcols[:, :, u, v]
+    return dxp[:, :, p:p + H, p:p + W], dw
+
+
+def logit_sensitivities(theta, x):
+    """Per stamp: the exact logits z (B,), the operand terms c = (dz/dv) v of
+    every BF16-rounded group {'w1','w2','w3','a1','a2'} (arrays (B, ...)),
+    and the FP32-accumulation magnitudes {'y1','y2','y3','pool','head'}
+    (B,): sum over the sums' outputs of |dz/dy| times sum |term| and the
+    term count n, as (magnitude, n) pairs."""
+    p = unpack(theta)
+    z, c = forward(theta, x, keep=True)
+    B = len(z)
+    HW = c["a3"].shape[2] * c["a3"].shape[3]
+    da3 = np.broadcast_to(p["wl"][None, :, None, None] / HW, c["a3"].shape)
+    dy3 = da3 * (c["y3"] > 0)
+    da2, dw3 = _conv_backward_per_stamp(c["a2"], p["w3"], dy3)
+    dy2 = da2 * (c["y2"] > 0)
+    da1, dw2 = _conv_backward_per_stamp(c["a1"], p["w2"], dy2)
+    dy1 = da1 * (c["y1"] > 0)
+    _, dw1 = _conv_backward_per_stamp(c["x"], p["w1"], dy1)
+    terms = {"w1": dw1 * p["w1"][None], "w2": dw2 * p["w2"][None], "w3": dw3 * p["w3"][None],
+             "a1": da1 * c["a1"], "a2": da2 * c["a2"]}
+    acc = {}
+    for name, dy, a_in, w, b in (("y1", dy1, c["x"], p["w1"], p["b1"]),
+                                 ("y2", dy2, c["a1"], p["w2"], p["b2"]),
+                                 ("y3", dy3, c["a2"], p["w3"], p["b3"])):
+        mag = _conv_abs(a_in, w) + np.abs(b)[None, :, None, None]
+        acc[name] = ((np.abs(dy) * mag).sum(axis=(1, 2, 3)), w.shape[1] * w.shape[2] * w.shape[3] + 1)
+    acc["pool"] = ((np.abs(p["wl"])[None, :] * c["a3"].mean(axis=(2, 3))).sum(axis=1), HW)
+    acc["head"] = (np.abs(c["g"] * p["wl"][None, :]).sum(axis=1) + abs(p["bl"][0]), p["wl"].size + 1)
+    return z, terms, acc
+
+
+def bf16_logit_bound(theta, x, lam=7.0, chunk=32):
+    """Per-stamp bound (B,) on |z~ - z| for a scorer with BF16 weights and
+    BF16 activations entering layers 2 and 3 and FP32 sums (see above):
+      lam u sqrt(sum_groups sum_i c_i^2) + sum_sums 2 n u32 |dz/dy| sum |term|.
+    Also returns the exact logits."""
+    x = np.asarray(x, np.float64)
+    zs, bounds = [], []
+    for s in range(0, len(x), chunk):
+        z, terms, acc = logit_sensitivities(theta, x[s:s + chunk])
+        ss = sum((t.reshape(len(z), -1) ** 2).sum(axis=1) for t in terms.values())
+        b32 = sum(2.0 * n * U_FP32 * m for m, n in acc.values())
+        zs.append(z)
+        bounds.append(lam * U_BF16 * np.sqrt(ss) + b32)
+    return np.concatenate(bounds), np.concatenate(zs)

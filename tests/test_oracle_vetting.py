@@ -138,3 +138,61 @@ def test_bf16_rounding_matches_library():
                         [1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -1.0 - 2.0 ** -8, 0.0, 1e-30]])
     ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
     np.testing.assert_array_equal(V.bf16_round(a), ref)
+
+
+def _perturbed_logits(theta, x, group, d):
+    """Logits with one operand group scaled by (1 + d): a weight tensor of a
+    layer or the activations entering layer 2 or 3 (built from the pinned
+    conv2d, not from forward())."""
+    p = V.unpack(theta)
+    w = {k: p[k] * (1 + d) if k == group else p[k] for k in ("w1", "w2", "w3")}
+    a1 = np.maximum(V.conv2d(x, w["w1"], p["b1"]), 0)
+    if group == "a1":
+        a1 = a1 * (1 + d)
+    a2 = np.maximum(V.conv2d(a1, w["w2"], p["b2"]), 0)
+    if group == "a2":
+        a2 = a2 * (1 + d)
+    a3 = np.maximum(V.conv2d(a2, w["w3"], p["b3"]), 0)
+    return a3.mean(axis=(2, 3)) @ p["wl"] + p["bl"][0]
+
+
+def _bound_case():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(6, 2, 21, 21))
+    x[:, 0, 8:13, 8:13] += 2.0
+    theta = V.init_params(2) + np.random.default_rng(3).normal(scale=0.02, size=V.N_PARAMS)
+    return theta, x
+
+
+def test_logit_sensitivities_predict_random_operand_roundings():
+    """For each rounded operand group, relative perturbations of +-u with
+    random signs move the exact logit by sum_i c_i d_i: its RMS over many
+    draws matches u sqrt(sum c_i^2) (a dropped, doubled or misplaced
+    sensitivity term fails this)."""
+    theta, x = _bound_case()
+    x = x[:2]
+    z, terms, _ = V.logit_sensitivities(theta, x)
+    np.testing.assert_allclose(z, V.forward(theta, x), rtol=1e-13)
+    rng = np.random.default_rng(7)
+    p = V.unpack(theta)
+    shapes = {"w1": p["w1"].shape, "w2": p["w2"].shape, "w3": p["w3"].shape,
+              "a1": (2, 32, 21, 21), "a2": (2, 32, 21, 21)}
+    for group, t in terms.items():
+        pred = V.U_BF16 * np.sqrt((t.reshape(2, -1) ** 2).sum(axis=1))
+        errs = []
+        for _ in range(60):
+            d = V.U_BF16 * rng.choice([-1.0, 1.0], size=shapes[group])
+            errs.append(_perturbed_logits(theta, x, group, d) - z)
+        rms = np.sqrt(np.mean(np.square(errs), axis=0))
+        assert np.all(np.abs(rms / pred - 1) < 0.3), (group, rms, pred)
+
+
+def test_bf16_bound_covers_a_bf16_rounded_network():
+    """The network with its weights and hidden activations rounded to BF16
+    (one concrete rounding pattern) stays inside the bound, and the bound is
+    a small fraction of the logits' spread (not vacuous)."""
+    theta, x = _bound_case()
+    bound, z = V.bf16_logit_bound(theta, x)
+    zb = V.forward(theta, x, bf16_operands=True)
+    assert np.all(np.abs(zb - z) <= bound)
+    assert np.median(bound) < 0.15 * np.sqrt(np.mean(z ** 2))
