@@ -31,13 +31,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "orbit×exposure samples/s and vetted candidates/s at fixed recall, plain vs chosen"
 UNIT = "samples/s"
-# FP64 peak of one GB300 derived from unit counts and clock: 152 SMs x 2 FP64
-# FMA per SM per clock x 2 flop x 2.07 GHz (the nominal 1.25 TFLOP/s).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# The stack kernel's bound: the FP64 pipe issues 2 thread-instructions per SM
-# per clock (152 SMs, 2.07 GHz), 629.3 G/s.  The roofline fraction is the
-# FP64-pipe time the launch needs (instructions per computed sample x computed
-# samples / that rate) over its measured time.
+# The stack kernel's bound is the FP64 pipe.  From unit counts it issues 2
+# thread-instructions per SM per clock (152 SMs, 2.07 GHz), 629.3 G/s; the
+# roofline's denominator is the rate measured at run time
+# (ndt_measure_fp64_rate), reported beside this derived figure.  The fraction
+# is the FP64-pipe time the launch needs (instructions per computed sample x
+# computed samples / that rate) over its measured time.
 FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 # FP64 flops executed per computed (orbit, exposure) sample by the stack
 # kernel, from ncu instruction counters (DFMA x 2 + DADD + DMUL) over the
@@ -48,6 +47,8 @@ FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 # MBA: 8.637e7 computed samples, 24.21 DFMA + 12.86 DMUL + 1.99 DADD each;
 # batched: 2.037e8 computed samples, 32.06 DFMA + 18.23 DMUL + 2.04 DADD.
 FP64_PER_SAMPLE = {"mba": (63.3, 39.6), "batched": (84.4, 53.3)}
+# The same counts split by instruction (DFMA, DMUL, DADD per computed sample).
+FP64_MIX = {"mba": (24.21, 12.86, 1.99), "batched": (32.06, 18.23, 2.04)}
 # DRAM bytes (read + write) of one full-size persistent stack launch (BF16
 # planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
 # in a one-pass capture: MBA 1.857 GB + 71.1 MB, batched 3.528 GB + 273.0 MB.
@@ -77,6 +78,8 @@ def parse():
     p.add_argument("--tiles", default=None, help="fixed OT,ET for the persistent form (no autotune)")
     p.add_argument("--no-vet", action="store_true", help="skip the CNN vetting stage")
     p.add_argument("--no-noise", action="store_true", help="skip the iterative-MAD noise timing")
+    p.add_argument("--no-batched", action="store_true",
+                   help="skip the batched uneven workload's sub-record (MBA runs only)")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
     p.add_argument("--vet-batch", type=int, default=1 << 20,
                    help="candidates of the separately timed vetting pass (0: skip)")
@@ -428,6 +431,8 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
         np_imgs = h_imgs.numpy()
         np_states = h_states.numpy()
 
+        stack_ms = []
+
         def run(n_steps):
             ndt.load_exposures(ctxs[0], sky.ex, np_imgs, plane_dtype=form.plane)
             for i in range(n_steps):
@@ -436,11 +441,13 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
                 if i + 1 < n_steps:                                                 # overlaps the stack
                     ndt.load_exposures(ctxs[(i + 1) % 2], sky.ex, np_imgs, plane_dtype=form.plane)
                 ndt.topk_candidates(c, k, h_idx[i % 2].numpy(), h_val[i % 2].numpy())
+                stack_ms.append(ndt.get_stats(c)["last_stack_ms"])   # c's stream is idle here
             return (n_steps - 1) % 2
 
         run(max(1, args.warmup))
         barrier()
         torch.cuda.synchronize(device)
+        stack_ms.clear()
         t0 = time.perf_counter()
         last = run(args.steps)
         torch.cuda.synchronize(device)
@@ -456,7 +463,8 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, k, form, barrier, device):
             "first": [[int(r), int(got[r]), int(ref_idx[r])] for r in diff[:4]],
             "device_recall_in_topk": recall_of(ref_idx, sky)}
     return dict(s_per_step=dt, h2d=h2d, d2h=d2h, recall_in_topk=recall_of(got, sky),
-                link_gbs=link_gbs, ranking_equals_device=same)
+                link_gbs=link_gbs, ranking_equals_device=same,
+                stack_ms=statistics.mean(stack_ms), stack_ms_max=max(stack_ms))
 
 
 # ------------------------------------------------------------ cpu oracle ----
@@ -552,6 +560,95 @@ def workload_name(args, sky, states):
 
 # ------------------------------------------------------------------- main ----
 
+def fp64_rates(device):
+    """Measured FP64 issue rates (G thread-instructions/s) of this GPU."""
+    from paper_2503_08854_gb300 import ndt
+    return {op: max(ndt.measure_fp64_rate(device.index, op) for _ in range(2)) / 1e9
+            for op in ("dfma", "dmul", "dadd")}
+
+
+def stack_roofline(workload, plane, res, rates):
+    """Roofline of the stack kernel: FP64-pipe instructions per computed sample
+    (ncu) x computed samples over the kernel's CUDA-event time, against the
+    measured DFMA issue rate; the instruction mix weighted by the measured
+    DFMA/DMUL/DADD rates gives the time bound the mix itself allows."""
+    samples = res["samples"]
+    stack_s = statistics.mean(res["stack_ms"]) / 1e3
+    flop, inst = FP64_PER_SAMPLE[workload]
+    n_fma, n_mul, n_add = FP64_MIX[workload]
+    computed = samples - res["skipped"]        # FP64 work runs only for these
+    gips = inst * computed / stack_s / 1e9
+    rest = inst - n_fma - n_mul - n_add        # conversions/compares: the DADD rate
+    mix_ns = n_fma / rates["dfma"] + (n_mul) / rates["dmul"] + (n_add + rest) / rates["dadd"]
+    peak_mix = inst / mix_ns
+    ach = flop * computed / stack_s / 1e12
+    return {"bound": "alu", "achieved": gips, "peak": rates["dfma"],
+            "unit": "G FP64-pipe thread-instructions/s", "frac": gips / rates["dfma"],
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(workload),
+            "kernel": "stack kernel (FP64 pipe)",
+            "peak_source": "measured: DFMA chains at full occupancy (ndt_measure_fp64_rate)",
+            "peak_derived_from_unit_counts": FP64_PIPE_PEAK_GIPS,
+            "fp64_rates_measured_gips": rates,
+            "peak_for_this_mix": peak_mix, "frac_of_mix_peak": gips / peak_mix,
+            "fp64_pipe_inst_per_sample": inst, "fp64_mix_per_sample": FP64_MIX[workload],
+            "fp64_tflops": ach, "fp64_samples_per_launch": computed,
+            "algorithmic_bytes_per_launch": (8 if plane == "f32" else 4) * res["valid"]}
+
+
+def form_record(res):
+    s = statistics.mean(res["step_ms"]) / 1e3
+    return {"samples_per_s": res["samples"] / s, "ms_per_step": s * 1e3,
+            "stack_ms": statistics.mean(res["stack_ms"]), "planes_ms": res["planes_ms"],
+            "topk_ms": res["topk_ms"], "recall": res["recall"],
+            "recall_in_topk": res["recall_topk"],
+            "valid_fraction": res["valid"] / max(res["samples"], 1),
+            "offchip_skipped_fraction": res["skipped"] / max(res["samples"], 1),
+            "tiles": res["tiles"]}
+
+
+def e2e_record(e2e, samples, world, max_over_ranks):
+    return {"value": samples * world / max_over_ranks(e2e["s_per_step"]), "unit": UNIT,
+            "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+            "recall_in_topk": e2e["recall_in_topk"],
+            "ms_per_step": e2e["s_per_step"] * 1e3,
+            "pipelined": "2 contexts: step i+1's host-to-device copies overlap step i's stack",
+            "h2d_link_gbs_untimed": e2e["link_gbs"],
+            "stack_ms_mean": e2e["stack_ms"], "stack_ms_max": e2e["stack_ms_max"],
+            "ranking_equals_device": e2e["ranking_equals_device"]}
+
+
+DTYPE = "f64 state; df32 light time and TAN; bf16 planes; f32 sums"
+
+
+def batched_subrecord(args, rank, device, barrier, world, max_over_ranks, rates):
+    """The batched uneven workload (4,096 families x 16,384 orbits, 20-400 of
+    400 exposures of 2048^2, BF16 planes) measured in the same run: both forms
+    and the chosen form's e2e, fewer steps than the headline."""
+    import copy
+    import torch
+    b = copy.copy(args)
+    b.workload, b.size, b.no_vet = "batched", 2048, True
+    b.steps, b.warmup = min(args.steps, 5), 3
+    sky, stream, imgs, states = make_workload(b, rank, device)
+    forms = {"chosen": Form("chosen", b.plane, "persistent", True),
+             "plain": Form("plain", "f32", "plain", False)}
+    out = {"workload": workload_name(b, sky, states), "steps": b.steps, "warmup": b.warmup}
+    res = {}
+    for name in ("chosen", "plain"):
+        r, e = bench_form(b, forms[name], sky, stream, imgs, states, device, barrier, None)
+        res[name] = r
+        out[name] = form_record(r)
+        if e is not None:
+            out["e2e"] = e2e_record(e, r["samples"], world, max_over_ranks)
+    r = res["chosen"]
+    out["value"] = r["samples"] * world / max_over_ranks(statistics.mean(r["step_ms"]) / 1e3)
+    out["unit"] = UNIT
+    out["roofline"] = stack_roofline("batched", b.plane, r, rates)
+    del imgs, states
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -582,6 +679,7 @@ def main():
     from paper_2503_08854_gb300 import __name__ as _pkg  # noqa: F401
     import __graft_entry__
     __graft_entry__.build()
+    rates = fp64_rates(device)
     vet_params, vet_info = None, None
     if args.workload == "batched":
         args.no_vet = True      # no injected sources to vet in the batched workload
@@ -600,7 +698,6 @@ def main():
         results[name] = res
         if e is not None:
             e2e = e
-    clk = clocks.stop()
     head = "chosen" if "chosen" in results else list(results)[0]
     r = results[head]
     samples = r["samples"]
@@ -609,7 +706,8 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE if forms[head].plane == "bf16"
+        else DTYPE.replace("bf16", forms[head].plane), "data": "synthetic",
         "config": {"workload": workload_name(args, sky, states),
                    "form": head, "planes": forms[head].plane,
                    "launch": forms[head].mode + ("+graph" if forms[head].graph else ""),
@@ -620,7 +718,6 @@ def main():
         "recall": r["recall"],
         "recall_def": f"injected asteroids whose family has an orbit with nu >= {RECALL_SNR}",
         "gpu_launches": int(r["launches"]),
-        "clocks": clk,
     }
     if vet_info is not None and r.get("vet_ms"):
         vet_info["vet_ms_per_step"] = statistics.mean(r["vet_ms"])
@@ -630,46 +727,20 @@ def main():
             vet_info["batch"] = r["vet_batch"]
         line["vetting"] = vet_info
     for name, res in results.items():
-        s = statistics.mean(res["step_ms"]) / 1e3
-        line[name] = {"samples_per_s": res["samples"] / s, "ms_per_step": s * 1e3,
-                      "stack_ms": statistics.mean(res["stack_ms"]), "planes_ms": res["planes_ms"],
-                      "topk_ms": res["topk_ms"], "recall": res["recall"],
-                      "recall_in_topk": res["recall_topk"],
-                      "valid_fraction": res["valid"] / max(res["samples"], 1),
-                      "offchip_skipped_fraction": res["skipped"] / max(res["samples"], 1)}
-    stack_s = statistics.mean(r["stack_ms"]) / 1e3
-    flop_per_sample, inst_per_sample = FP64_PER_SAMPLE[args.workload]
-    # FP64 work runs only for the samples the off-chip test did not remove
-    computed = samples - r["skipped"]
-    if flop_per_sample is not None:
-        ach = flop_per_sample * computed / stack_s / 1e12
-        gips = inst_per_sample * computed / stack_s / 1e9
-        line["roofline"] = {"bound": "alu", "achieved": gips, "peak": FP64_PIPE_PEAK_GIPS,
-                            "unit": "G FP64-pipe thread-instructions/s", "frac": gips / FP64_PIPE_PEAK_GIPS,
-                            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(args.workload),
-                            "kernel": "stack kernel (FP64 pipe)",
-                            "fp64_pipe_inst_per_sample": inst_per_sample,
-                            "fp64_tflops": ach, "fp64_tflops_frac_of_1.259": ach / FP64_PEAK_TFLOPS,
-                            "fp64_samples_per_launch": computed,
-                            "algorithmic_bytes_per_launch":
-                                (8 if forms[head].plane == "f32" else 4) * r["valid"]}
-    else:
-        line["roofline"] = {"bound": "alu", "achieved": None, "peak": FP64_PIPE_PEAK_GIPS,
-                            "unit": "G FP64-pipe thread-instructions/s", "frac": None, "traffic": None,
-                            "note": "FP64 instructions per sample not yet measured",
-                            "stack_samples_per_s": samples / stack_s}
+        line[name] = form_record(res)
+    line["roofline"] = stack_roofline(args.workload, forms[head].plane, r, rates)
     if e2e is not None:
-        line["e2e"] = {"value": samples * world / max_over_ranks(e2e["s_per_step"]), "unit": UNIT,
-                       "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
-                       "recall_in_topk": e2e["recall_in_topk"],
-                       "ms_per_step": e2e["s_per_step"] * 1e3,
-                       "pipelined": "2 contexts: step i+1's host-to-device copies overlap step i's stack",
-                       "h2d_link_gbs_untimed": e2e["link_gbs"],
-                       "ranking_equals_device": e2e["ranking_equals_device"]}
+        line["e2e"] = e2e_record(e2e, samples, world, max_over_ranks)
     if rank == 0 and args.workload == "mba" and not args.no_noise:
         line["noise_estimate"] = noise_rate(device, stream, imgs)
-    if rank == 0 and not args.no_cpu:
-        host = imgs.cpu().numpy()
+    host = imgs.cpu().numpy() if rank == 0 and not args.no_cpu else None
+    if args.workload == "mba" and not args.no_batched:
+        del imgs, states
+        torch.cuda.empty_cache()
+        line["batched"] = batched_subrecord(args, rank, device, barrier, world, max_over_ranks,
+                                            rates)
+    line["clocks"] = clocks.stop()
+    if host is not None:
         rate, cores, desc = cpu_oracle_rate(sky, host, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": desc}

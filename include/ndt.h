@@ -366,6 +366,16 @@ ndt_status ndt_selftest_wait_timeout(ndt_ctx *ctx);
 ndt_status ndt_topk_noalloc(const float *snr_dev, int64_t n, int64_t k, int64_t *idx_out,
                             float *snr_out, void *cuda_stream);
 
+/* Measured issue rate of the FP64 pipe on `device` (no counterpart in the
+   paper; the denominator of the stacking kernel's roofline, which is bound
+   by FP64 instructions).  op 0 = DFMA, 1 = DMUL, 2 = DADD: every thread of a
+   full-occupancy grid runs eight independent chains of that instruction;
+   *inst_per_s = thread-instructions retired per second over four launches
+   (after one warm-up launch), *seconds (may be NULL) = their duration.
+   Allocates and frees a small output buffer; synchronous on the legacy
+   default stream.  NDT_EINVAL for a bad op or device. */
+ndt_status ndt_measure_fp64_rate(int device, int32_t op, double *inst_per_s, double *seconds);
+
 /* Copy the context's counters into *out. */
 ndt_status ndt_get_stats(ndt_ctx *ctx, ndt_stats *out);
 

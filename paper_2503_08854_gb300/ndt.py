@@ -78,6 +78,7 @@ _lib.ndt_cnn_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i32, C.c_floa
 _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 _lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
+_lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
 
 class NdtError(RuntimeError):
@@ -300,6 +301,17 @@ def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
         raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
 
 
+def measure_fp64_rate(device, op="dfma"):
+    """ndt_measure_fp64_rate: FP64 thread-instructions per second the GPU
+    sustains for one instruction kind ("dfma", "dmul" or "dadd")."""
+    code = {"dfma": 0, "dmul": 1, "dadd": 2}[op]
+    rate, sec = C.c_double(), C.c_double()
+    st = _lib.ndt_measure_fp64_rate(int(device), code, C.byref(rate), C.byref(sec))
+    if st != OK:
+        raise NdtError(st, "ndt_measure_fp64_rate failed")
+    return rate.value
+
+
 def exported_symbols():
     """Names of the C entry points this binding uses (all must be exported)."""
     return ["ndt_create", "ndt_destroy", "ndt_last_error", "ndt_set_constants",
@@ -309,4 +321,5 @@ def exported_symbols():
             "ndt_autotune",
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
-            "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc"]
+            "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
+            "ndt_measure_fp64_rate"]
