@@ -64,7 +64,7 @@ struct ndt_ctx {
   std::vector<int32_t> sorted_to_table, table_to_sorted;
   std::vector<ExpDev> ex_host;
   int plane_type = kF32;
-  DevBuf ex_dev, pos_to_table_dev, planes, jobs_dev, absmax_dev;
+  DevBuf ex_dev, pos_to_table_dev, planes, jobs_dev, absmax_dev, plane_err;
   DevBuf stage_images, stage_vars;
   // orbit batch
   DevBuf stage_states, snr, out_tmp, xy_tmp;
@@ -322,7 +322,7 @@ void ndt_destroy(ndt_ctx* c) {
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   DevBuf* bufs[] = {&c->ex_dev, &c->pos_to_table_dev, &c->planes, &c->jobs_dev,
-                    &c->absmax_dev, &c->stage_images, &c->stage_vars,
+                    &c->absmax_dev, &c->plane_err, &c->stage_images, &c->stage_vars,
                     &c->stage_states, &c->snr, &c->out_tmp, &c->xy_tmp, &c->fam_orb_off,
                     &c->fam_exp_off, &c->fam_exp_pos, &c->item_off, &c->fam_order,
                     &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
@@ -391,7 +391,6 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
   std::vector<PlaneJob> jobs(n_exp);
   std::vector<double> sum_p2(n_exp);   // sum of P^2 over the PSF window
   int64_t plane_elems = 0, img_elems = 0;
-  int max_tiles = 0;
   for (int s = 0; s < n_exp; ++s) {
     const ndt_exposure& m = meta[ctx->sorted_to_table[s]];
     ExpDev& e = ctx->ex_host[s];
@@ -412,7 +411,6 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     e.s_psi = 1.0f;
     e.s_phi = 1.0f;
     plane_elems += (int64_t)e.tiles_x * tiles_y * kTile * kTile;
-    max_tiles = std::max(max_tiles, planes_ctas_per_job(e.tiles_x, tiles_y));
     PlaneJob& J = jobs[s];
     J.var_c = m.variance > 0.0f ? m.variance : 1.0f;
     J.sigma = filter_sigma(ctx, m.psf_sigma_px);
@@ -508,22 +506,26 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
       ctx->noise_sigma[ctx->sorted_to_table[s]] = sg;
     }
   }
+  int max_R = 0;
+  for (const PlaneJob& J : jobs) max_R = std::max(max_R, J.R);
+  plane_jobs_prepare(jobs.data(), n_exp, max_R);
   NDT_CK(ctx->jobs_dev.ensure(sizeof(PlaneJob) * n_exp), "job table");
   NDT_CK(cudaMemcpyAsync(ctx->jobs_dev.p, jobs.data(), sizeof(PlaneJob) * n_exp,
                          cudaMemcpyHostToDevice, ctx->stream), "job upload");
-  int max_R = 0;
-  for (const PlaneJob& J : jobs) max_R = std::max(max_R, J.R);
+  NDT_CK(ctx->plane_err.ensure(4), "plane error word");
+  NDT_CK(cudaMemsetAsync(ctx->plane_err.p, 0, 4, ctx->stream), "memset");
+  unsigned int* perr = ctx->plane_err.as<unsigned int>();
   const bool any_var = variances != nullptr;
   const size_t pair_bytes = plane_dtype == NDT_PLANE_F32 ? 8 : 4;
   NDT_CK(ctx->planes.ensure(pair_bytes * plane_elems), "plane allocation");
   record(ctx, 0);
   if (plane_dtype == NDT_PLANE_F32) {
-    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneStoreF32,
-                         ctx->planes.p, nullptr, ctx->stream), "plane kernel");
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), jobs.data(), n_exp, max_R, any_var, kPlaneStoreF32,
+                         ctx->planes.p, nullptr, perr, ctx->stream), "plane kernel");
     ctx->launches += 1;
   } else if (plane_dtype == NDT_PLANE_BF16) {
-    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var,
-                         kPlaneStoreBF16, ctx->planes.p, nullptr, ctx->stream), "plane kernel");
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), jobs.data(), n_exp, max_R, any_var,
+                         kPlaneStoreBF16, ctx->planes.p, nullptr, perr, ctx->stream), "plane kernel");
     ctx->launches += 1;
     for (int s = 0; s < n_exp; ++s) {
       ctx->ex_host[s].s_psi = jobs[s].s_psi;
@@ -534,11 +536,12 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     // same planes again, written as FP16 pairs scaled by those maxima
     NDT_CK(ctx->absmax_dev.ensure(8 * n_exp), "absmax");
     NDT_CK(cudaMemsetAsync(ctx->absmax_dev.p, 0, 8 * n_exp, ctx->stream), "memset");
-    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var, kPlaneAbsMax, nullptr,
-                         ctx->absmax_dev.as<unsigned int>(), ctx->stream), "plane max kernel");
-    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), n_exp, max_tiles, max_R, any_var,
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), jobs.data(), n_exp, max_R, any_var, kPlaneAbsMax,
+                         nullptr, ctx->absmax_dev.as<unsigned int>(), perr, ctx->stream),
+           "plane max kernel");
+    NDT_CK(launch_planes(ctx->jobs_dev.as<PlaneJob>(), jobs.data(), n_exp, max_R, any_var,
                          kPlaneStoreF16,
-                         ctx->planes.p, ctx->absmax_dev.as<unsigned int>(), ctx->stream),
+                         ctx->planes.p, ctx->absmax_dev.as<unsigned int>(), perr, ctx->stream),
            "plane kernel");
     ctx->launches += 2;
   }
@@ -563,8 +566,13 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
   NDT_CK(ctx->pos_to_table_dev.ensure(4 * n_exp), "permutation");
   NDT_CK(cudaMemcpyAsync(ctx->pos_to_table_dev.p, ctx->sorted_to_table.data(), 4 * n_exp,
                          cudaMemcpyHostToDevice, ctx->stream), "permutation upload");
+  unsigned int plane_err_h = 0;
+  NDT_CK(cudaMemcpyAsync(&plane_err_h, perr, 4, cudaMemcpyDeviceToHost, ctx->stream), "error read-back");
   // host vectors above must outlive the async copies
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (plane_err_h != 0)
+    return fail(ctx, NDT_ETIMEOUT, "planes kernel: %u TMA loads did not arrive within the wait limit",
+                plane_err_h);
   ctx->plane_type = plane_dtype;
   ctx->n_exp = n_exp;
   ctx->last_n = 0;

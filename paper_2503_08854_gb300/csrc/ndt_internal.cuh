@@ -10,6 +10,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -600,6 +601,12 @@ __device__ __forceinline__ float2 gather_plane(const void* __restrict__ planes, 
 // Launchers (defined in the kernel translation units).
 // ---------------------------------------------------------------------------
 struct PlaneJob {
+  // TMA descriptor of the image (2-D, W x H FP32, zero fill outside) when
+  // `tma` != 0 (the window radius its box was encoded for): constant
+  // variance, W a multiple of 4, 16-byte aligned image
+  CUtensorMap tmap;     // 128-byte aligned by its own declaration
+  int32_t tma;
+  int32_t n_strips;     // TMA form: strips of 4 tiles (0 for the general form)
   const float* image;   // row-major H x W
   const float* var;     // row-major H x W, or null (constant variance)
   float var_c;
@@ -610,6 +617,7 @@ struct PlaneJob {
   float s_psi, s_phi;   // a-priori scales of the BF16 planes (noise sigma of psi, interior phi)
   float g[2 * kMaxPsfRadius + 1];    // unit-sum 1-D Gaussian window (host FP64, rounded)
   float g2[2 * kMaxPsfRadius + 1];   // its square
+  float pre[2 * kMaxPsfRadius + 2];  // pre[i] = sum of g2 over taps < i (FP32, in order)
 };
 
 // Plane kernel outputs: FP32 pairs, or (two passes) the largest |psi| and phi
@@ -618,9 +626,18 @@ enum PlaneMode : int32_t { kPlaneStoreF32 = 0, kPlaneAbsMax = 1, kPlaneStoreBF16
 
 // CTAs of the planes kernel per exposure of tiles_x x tiles_y tiles; a launch
 // takes the largest over its exposures as grid.x ("max_ctas" below).
-int planes_ctas_per_job(int tiles_x, int tiles_y);
-cudaError_t launch_planes(const PlaneJob* jobs_dev, int n_jobs, int max_ctas, int max_R, bool any_var,
-                          int mode, void* out, unsigned int* absmax2, cudaStream_t st);
+// Fill J.tmap and set J.tma (to the launch's window radius, from max_R of
+// all jobs) when the job can take the TMA form (constant variance, W % 4 ==
+// 0, 16-byte aligned image, TMA available); else J.tma = 0.
+void plane_job_try_tma(PlaneJob& J, int max_R);
+// plane_job_try_tma for every job, its strip count and prefix sums of g^2.
+void plane_jobs_prepare(PlaneJob* jobs, int n_jobs, int max_R);
+// Launch the planes of every job: the TMA form for jobs with J.tma set, the
+// general form for the others.  `jobs_host` mirrors `jobs_dev`; `err` (device
+// word, zeroed by the caller) counts CTAs whose bounded TMA wait gave up.
+cudaError_t launch_planes(const PlaneJob* jobs_dev, const PlaneJob* jobs_host, int n_jobs, int max_R,
+                          bool any_var, int mode, void* out, unsigned int* absmax2,
+                          unsigned int* err, cudaStream_t st);
 cudaError_t launch_plane_decode(const void* planes, int plane_type, const ExpDev* e_host_copy,
                                 float* psi, float* phi, cudaStream_t st);
 

@@ -1,6 +1,7 @@
 // tc_ptx.cuh -- thin inline-PTX wrappers for the 5th-generation tensor core
-// (tcgen05: MMA with accumulators in tensor memory), mbarriers and the proxy
-// fences they need, as used by k_cnn_tc.cu.  sm_100-family only.
+// (tcgen05: MMA with accumulators in tensor memory), the tensor memory
+// accelerator (TMA tiled loads), mbarriers and the proxy fences they need, as
+// used by k_cnn_tc.cu and k_planes.cu.  sm_100-family only.
 #pragma once
 
 #include <cstdint>
@@ -41,6 +42,33 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (i > 64) __nanosleep(128);
   }
   return false;
+}
+
+// Arrive on `bar` (one of its expected arrivals) and add `bytes` to the
+// transaction count that asynchronous copies must complete in this phase.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// ---- TMA ----------------------------------------------------------------------
+// Make the host-written tensor map at `tmap` (global memory) visible to the
+// tensor-map proxy before its first use in this kernel.
+__device__ __forceinline__ void tmap_acquire(const void* tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
+// 2-D tiled load of the tensor map's box at element coordinates (x, y) (x the
+// innermost; x * element size must be a multiple of 16 bytes; out-of-range
+// elements read as zero) into shared memory at `dst`, completing `bar`'s
+// transaction bytes.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int32_t x, int32_t y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
 // ---- fences -----------------------------------------------------------------

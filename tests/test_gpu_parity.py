@@ -67,6 +67,34 @@ def test_planes_match_oracle(gpu, per_pixel_var):
         np.testing.assert_allclose(phi, rf, rtol=1e-5, atol=1e-7 * np.abs(rf).max())
 
 
+@pytest.mark.parametrize("plane", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("wide_psf", [False, True])
+def test_planes_both_kernel_forms_match_oracle(gpu, plane, wide_psf):
+    """Exposures of one load split between the TMA form (widths a multiple of
+    4 px) and the general form (other widths), ragged tiles on both axes, a
+    one-row image and a 4-pixel-wide one; PSF windows of R <= 8 or, with
+    a wide PSF, up to R = 16 (the other compile-time window)."""
+    rng = np.random.default_rng(7)
+    sky = _ragged_sky(n_exp=6)
+    ex = sky.ex.subset(range(6))
+    ex.width = np.array([132, 37, 200, 4, 70, 260], np.int32)
+    ex.height = np.array([70, 65, 1, 64, 33, 97], np.int32)
+    ex.sigma = np.array([1.3, 1.9, 2.0, 0.6, 1.2, 3.9 if wide_psf else 1.7])
+    imgs = [rng.normal(size=(ex.height[j], ex.width[j])).astype(np.float32) for j in range(6)]
+    d = [torch.from_numpy(im).to(gpu.dev) for im in imgs]
+    torch.cuda.synchronize()
+    ndt.load_exposures(gpu.ctx, ex, d, plane_dtype=plane)
+    rel = {"f32": 0.0, "bf16": 2.0 ** -8, "f16": 2.0 ** -11}[plane]
+    for j in range(6):
+        psi, phi = gpu.planes(j, ex.height[j], ex.width[j])
+        rp, rf = O.planes(imgs[j], ex.sigma[j], ex.var[j])
+        s = np.abs(rp).max() / 16384 if plane == "f16" else 0.0
+        tol_psi = rel * np.abs(rp) + s * 2.0 ** -14 + 1e-5 * np.abs(rp) + 2e-6 * np.abs(rp).max()
+        tol_phi = rel * np.abs(rf) + 1e-5 * np.abs(rf) + 1e-7 * rf.max()
+        assert np.all(np.abs(psi - rp) <= tol_psi), (j, np.abs(psi - rp).max())
+        assert np.all(np.abs(phi - rf) <= tol_phi), (j, np.abs(phi - rf).max())
+
+
 @pytest.mark.parametrize("plane", ["bf16", "f16"])
 def test_reduced_precision_planes_error_bound(gpu, plane):
     """RNE of value/scale: |error| <= half an ulp of the stored format (2^-9
