@@ -325,6 +325,29 @@ ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, in
                                const int64_t *cand_idx, int64_t n_cand, float kappa, int32_t max_iter,
                                int32_t min_obs, float *nu_out, int32_t *nkept_out);
 
+/*
+ * dedup_candidates: drop near-duplicate candidates from a ranked list (no
+ * counterpart in the paper, whose detections come one orbit at a time; a
+ * dense search finds every object through many neighbouring orbits, and
+ * this reading removes them so that the list holds one entry per track).
+ * cand_idx (n_cand indices into the orbit batch `states`, SoA 6 x n_orbits at
+ * t0, host or device) is taken in rank order, best first, e.g. the output of
+ * ndt_topk_candidates.  n_ref reference exposures are spread evenly over the
+ * epoch-sorted exposures (first and last included); candidate i is a
+ * duplicate when some candidate ranked before it has predicted pixel
+ * positions (same propagation, light time and TAN projection as the stack)
+ * within radius_px of i's at every reference exposure, each in that
+ * exposure's own pixel grid.  The kept indices are written in rank order to
+ * keep_idx (host or device, n_cand entries of room), their number to
+ * *n_keep (host).  Candidates whose middle reference position is undefined
+ * (tangent point 90 degrees or more away) are kept.  radius_px > 0 and
+ * finite, 1 <= n_ref <= 8, 0 <= n_cand <= 2^26, else NDT_EINVAL; NDT_ESTATE
+ * before load_exposures.  Synchronous.
+ */
+ndt_status ndt_dedup_candidates(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
+                                const int64_t *cand_idx, int64_t n_cand, float radius_px, int32_t n_ref,
+                                int64_t *keep_idx, int64_t *n_keep);
+
 /* vet: stamps of the candidates (as ndt_stamps) scored by the network:
    scores[i] = sigmoid(logit) in [0, 1]. */
 ndt_status ndt_vet(ndt_ctx *ctx, const float *params, const double *states, double t0,

@@ -77,6 +77,8 @@ struct ndt_ctx {
   // vetting
   DevBuf cand_stage, stamp_pos, stamp_f32, stamp_bf16, cnn_x, cnn_labels, cnn_out, cnn_scratch,
       cnn_params, cnn_grad, trim_bits, trim_nu, trim_n;
+  // duplicate suppression
+  DevBuf dedup_scratch, dedup_ref, dedup_out;
   // noise estimate
   DevBuf mad_imgs, mad_state, mad_hist, mad_stage;
   std::vector<float> noise_sigma;   // per exposure (table order): estimated sigma, or 0 if given
@@ -328,6 +330,7 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
                     &c->cand_stage, &c->stamp_pos, &c->stamp_f32, &c->stamp_bf16, &c->cnn_x,
                     &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad,
+                    &c->dedup_scratch, &c->dedup_ref, &c->dedup_out,
                     &c->trim_bits, &c->trim_nu, &c->trim_n, &c->mad_imgs, &c->mad_state,
                     &c->mad_hist, &c->mad_stage};
   for (DevBuf* b : bufs) b->release();
@@ -1010,6 +1013,58 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
 }  // namespace
 
 extern "C" {
+
+ndt_status ndt_dedup_candidates(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
+                                const int64_t* cand_idx, int64_t n_cand, float radius_px, int32_t n_ref,
+                                int64_t* keep_idx, int64_t* n_keep) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "dedup before load_exposures");
+  if (!n_keep) return fail(ctx, NDT_EINVAL, "n_keep is null");
+  if (n_orbits < 0 || n_cand < 0 || n_cand > (int64_t(1) << 26) ||
+      (n_cand > 0 && (!states || !cand_idx || !keep_idx)))
+    return fail(ctx, NDT_EINVAL, "bad dedup arguments");
+  if (!(radius_px > 0.0f) || !std::isfinite(radius_px) || n_ref < 1 || n_ref > 8)
+    return fail(ctx, NDT_EINVAL, "radius %g or n_ref %d out of range", radius_px, n_ref);
+  *n_keep = 0;
+  if (n_cand == 0) return NDT_OK;
+  // reference exposures: evenly spread over the epoch-sorted exposures
+  std::vector<int32_t> ref;
+  for (int k = 0; k < n_ref; ++k) {
+    const int32_t pos = n_ref == 1 ? (ctx->n_exp - 1) / 2
+                                   : (int32_t)std::lround((double)k * (ctx->n_exp - 1) / (n_ref - 1));
+    if (ref.empty() || pos > ref.back()) ref.push_back(pos);
+  }
+  const int nr = (int)ref.size();
+  const void* st_dev = nullptr;
+  ndt_status s = to_device(ctx, states, sizeof(double) * 6 * n_orbits, ctx->stage_states, &st_dev);
+  if (s != NDT_OK) return s;
+  const void* cd = nullptr;
+  if ((s = to_device(ctx, cand_idx, sizeof(int64_t) * n_cand, ctx->cand_stage, &cd)) != NDT_OK) return s;
+  int64_t* out = nullptr;
+  if ((s = out_buffer(ctx, keep_idx, n_cand, ctx->dedup_out, &out)) != NDT_OK) return s;
+  NDT_CK(ctx->dedup_ref.ensure(sizeof(int32_t) * nr + 16), "dedup references");
+  NDT_CK(ctx->dedup_scratch.ensure(dedup_scratch_bytes(n_cand, nr, dedup_table_size(n_cand))),
+         "dedup scratch");
+  NDT_CK(cudaMemcpyAsync(ctx->dedup_ref.p, ref.data(), sizeof(int32_t) * nr, cudaMemcpyHostToDevice,
+                         ctx->stream), "upload");
+  int* n_keep_dev = reinterpret_cast<int*>(static_cast<unsigned char*>(ctx->dedup_ref.p) +
+                                           ((sizeof(int32_t) * nr + 3) / 4) * 4);
+  NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
+  NDT_CK(launch_dedup(static_cast<const double*>(st_dev), n_orbits, t0, static_cast<const int64_t*>(cd),
+                      n_cand, ctx->ex_dev.as<ExpDev>(), ctx->dedup_ref.as<int32_t>(), nr, ctx->ph, radius_px,
+                      ctx->dedup_scratch.p, ctx->counters.as<unsigned long long>(), out, n_keep_dev,
+                      ctx->stream),
+         "dedup kernels");
+  ctx->launches += 6;
+  int nk = 0;
+  NDT_CK(cudaMemcpyAsync(&nk, n_keep_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if ((s = copy_out(ctx, keep_idx, out, (size_t)nk)) != NDT_OK) return s;
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  *n_keep = nk;
+  return NDT_OK;
+}
 
 ndt_status ndt_selftest_wait_timeout(ndt_ctx* ctx) {
   if (!ctx) return NDT_EINVAL;

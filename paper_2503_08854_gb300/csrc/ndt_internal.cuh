@@ -678,6 +678,14 @@ cudaError_t launch_predict(const double* states, int64_t n, double t0, const Exp
                            const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph,
                            double* xy, unsigned long long* counters, cudaStream_t st);
 
+// duplicate suppression of ranked candidates (k_dedup.cu)
+uint32_t dedup_table_size(int64_t n_cand);
+size_t dedup_scratch_bytes(int64_t n_cand, int n_ref, uint32_t table);
+cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64_t* cand, int64_t n_cand,
+                         const ExpDev* ex, const int32_t* ref_dev, int n_ref, Phys ph, float radius,
+                         void* scratch, unsigned long long* counters, int64_t* out, int* n_keep_dev,
+                         cudaStream_t st);
+
 // vetting (stamps + CNN)
 int cnn_param_count();
 size_t cnn_smem_bytes();

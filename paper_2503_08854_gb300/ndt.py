@@ -78,6 +78,7 @@ _lib.ndt_cnn_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i32, C.c_floa
 _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 _lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
+_lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _vp, C.POINTER(_i64)]
 _lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
 
@@ -301,6 +302,17 @@ def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
         raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
 
 
+def dedup_candidates(ctx, states_soa, t0, n_orbits, cand_idx, n_cand, keep_idx, radius_px=4.0, n_ref=3):
+    """ndt_dedup_candidates: keep_idx[:returned] = the candidates of cand_idx
+    (rank order) with no better-ranked candidate within radius_px at every
+    reference exposure; returns that number."""
+    nk = C.c_int64()
+    _check(ctx, _lib.ndt_dedup_candidates(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(cand_idx),
+                                          int(n_cand), float(radius_px), int(n_ref), _ptr(keep_idx),
+                                          C.byref(nk)))
+    return nk.value
+
+
 def measure_fp64_rate(device, op="dfma"):
     """ndt_measure_fp64_rate: FP64 thread-instructions per second the GPU
     sustains for one instruction kind ("dfma", "dmul" or "dadd")."""
@@ -322,4 +334,4 @@ def exported_symbols():
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
-            "ndt_measure_fp64_rate"]
+            "ndt_measure_fp64_rate", "ndt_dedup_candidates"]
