@@ -189,6 +189,13 @@ ndt_status ndt_topk_candidates(ndt_ctx *ctx, int64_t k, int64_t *idx_out, float 
  * tangent point is 90 degrees or more away (cos c <= 0).  j follows the
  * order of the table given to load_exposures.  FP64, n_orbits * n_exp * 2.
  */
+/* count_candidates: the number of orbits of the last stack whose nu is at
+   least min_snr (the detection threshold of Algorithm 1,
+   FindSignificantResults; NaN and -inf never count), into *count (host).
+   Sized for ndt_topk_candidates with that k.  NDT_ESTATE without a stacked
+   batch, NDT_EINVAL for a NaN threshold or a null count.  Synchronous. */
+ndt_status ndt_count_candidates(ndt_ctx *ctx, float min_snr, int64_t *count);
+
 ndt_status ndt_predict_positions(ndt_ctx *ctx, const double *states, double t0,
                                  int64_t n_orbits, double *xy_out);
 
@@ -339,8 +346,9 @@ ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, in
  * within radius_px of i's at every reference exposure, each in that
  * exposure's own pixel grid.  The kept indices are written in rank order to
  * keep_idx (host or device, n_cand entries of room), their number to
- * *n_keep (host).  Candidates whose middle reference position is undefined
- * (tangent point 90 degrees or more away) are kept.  radius_px > 0 and
+ * *n_keep (host).  A position is undefined where the exposure's tangent
+ * point is 90 degrees or more away: such a candidate is within radius_px of
+ * no other, so it is kept and removes nothing.  radius_px > 0 and
  * finite, 1 <= n_ref <= 8, 0 <= n_cand <= 2^26, else NDT_EINVAL; NDT_ESTATE
  * before load_exposures.  Synchronous.
  */

@@ -78,7 +78,7 @@ struct ndt_ctx {
   DevBuf cand_stage, stamp_pos, stamp_f32, stamp_bf16, cnn_x, cnn_labels, cnn_out, cnn_scratch,
       cnn_params, cnn_grad, trim_bits, trim_nu, trim_n;
   // duplicate suppression
-  DevBuf dedup_scratch, dedup_ref, dedup_out;
+  DevBuf dedup_scratch, dedup_ref, dedup_out, count_dev;
   // noise estimate
   DevBuf mad_imgs, mad_state, mad_hist, mad_stage;
   std::vector<float> noise_sigma;   // per exposure (table order): estimated sigma, or 0 if given
@@ -330,7 +330,7 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->queue_head, &c->counters, &c->topk_scratch, &c->topk_out,
                     &c->cand_stage, &c->stamp_pos, &c->stamp_f32, &c->stamp_bf16, &c->cnn_x,
                     &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad,
-                    &c->dedup_scratch, &c->dedup_ref, &c->dedup_out,
+                    &c->dedup_scratch, &c->dedup_ref, &c->dedup_out, &c->count_dev,
                     &c->trim_bits, &c->trim_nu, &c->trim_n, &c->mad_imgs, &c->mad_state,
                     &c->mad_hist, &c->mad_stage};
   for (DevBuf* b : bufs) b->release();
@@ -825,6 +825,22 @@ ndt_status ndt_topk_candidates(ndt_ctx* ctx, int64_t k, int64_t* idx_out, float*
   if (h_idx) NDT_CK(cudaMemcpyAsync(idx_out, di, 8 * k, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
   if (h_snr) NDT_CK(cudaMemcpyAsync(snr_out, ds, 4 * k, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return NDT_OK;
+}
+
+ndt_status ndt_count_candidates(ndt_ctx* ctx, float min_snr, int64_t* count) {
+  if (!ctx) return NDT_EINVAL;
+  NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->last_n <= 0) return fail(ctx, NDT_ESTATE, "count_candidates without a stacked batch");
+  if (!count || std::isnan(min_snr)) return fail(ctx, NDT_EINVAL, "bad count arguments");
+  NDT_CK(ctx->count_dev.ensure(8), "count");
+  NDT_CK(launch_count_ge(ctx->snr.as<float>(), ctx->last_n, min_snr, ctx->count_dev.as<unsigned long long>(),
+                         ctx->stream), "count kernel");
+  ctx->launches += 1;
+  unsigned long long c = 0;
+  NDT_CK(cudaMemcpyAsync(&c, ctx->count_dev.p, 8, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
+  NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
+  *count = (int64_t)c;
   return NDT_OK;
 }
 

@@ -10,11 +10,19 @@
 //
 // Positions come from the same propagation, light time and double-float TAN
 // projection as the stack (chained universal-variable steps through the
-// reference epochs).  Neighbours are found through a hash grid of cell size
-// r on the middle reference exposure: two tracks within r there lie in the
-// same or adjacent cells, so every candidate scans the lists of 9 cells; a
-// list holds the candidates of every cell that hashes to its bucket, and the
-// distance test sorts them out.
+// reference epochs).  Neighbours are found through a hash grid over the
+// positions at the first and last reference exposures (four coordinates;
+// the middle one alone when n_ref = 1) with cells of size 2r: a track within
+// r of candidate i lies, in each coordinate, in i's cell or in the adjacent
+// cell on the side of the half that i occupies, so 2^4 buckets hold every
+// possible duplicate.  The candidates are sorted by (bucket, rank) with the
+// stable radix sort of the ranking, so each bucket is a run in rank order; a
+// candidate scans the runs of its 16 buckets only up to its own rank and
+// stops at the first better-ranked candidate within r at every reference (a
+// bucket also holds the candidates of other cells that hash to it: the
+// distance test sorts them out).  A candidate with an undefined position at
+// some reference exposure is within r of nothing: it is kept and never
+// inserted.
 #include <climits>
 #include <cstdint>
 
@@ -90,52 +98,94 @@ __global__ void __launch_bounds__(kDedupThreads)
   }
 }
 
-__device__ __forceinline__ bool cell_of(float2 p, float inv_cell, int& cx, int& cy) {
-  if (!(fabsf(p.x) < 1e9f && fabsf(p.y) < 1e9f)) return false;   // NaN or far beyond any chip
-  cx = (int)floorf(p.x * inv_cell);
-  cy = (int)floorf(p.y * inv_cell);
+// Hash-grid coordinates of a candidate: the cells (size 2r) of its
+// positions at the key references, and per coordinate the side (-1 or +1) of
+// the neighbouring cell that a track within r can fall into.  False when a
+// position at any reference is undefined (or absurdly far off the chip).
+struct GridKey {
+  int c[4];
+  int side[4];
+};
+
+__device__ __forceinline__ bool grid_key(const float2* p, int n_ref, float inv_cell2, GridKey& g) {
+  for (int k = 0; k < n_ref; ++k)
+    if (!(fabsf(p[k].x) < 1e9f && fabsf(p[k].y) < 1e9f)) return false;
+  // first and last references; with one reference its position, the other
+  // two coordinates zero (one cell)
+  const float2 a = p[0], b = n_ref == 1 ? make_float2(0.0f, 0.0f) : p[n_ref - 1];
+  const float v[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+  for (int d = 0; d < 4; ++d) {
+    const float q = v[d] * inv_cell2;
+    const float f = floorf(q);
+    g.c[d] = (int)f;
+    g.side[d] = q - f < 0.5f ? -1 : 1;
+  }
   return true;
 }
 
-__device__ __forceinline__ uint32_t cell_hash(int cx, int cy, uint32_t mask) {
-  return ((uint32_t)cx * 73856093u ^ (uint32_t)cy * 19349663u) & mask;
+__device__ __forceinline__ uint32_t key_hash(const int c[4], uint32_t mask) {
+  uint32_t h = (uint32_t)c[0] * 73856093u;
+  h ^= (uint32_t)c[1] * 19349663u;
+  h ^= (uint32_t)c[2] * 83492791u;
+  h ^= (uint32_t)c[3] * 2654435761u;
+  return (h ^ (h >> 15)) & mask;
 }
 
-// Lists of candidates per hash bucket of their middle-reference cell.
+// items[i] = (bucket of i's own cell) << 32 | i; candidates with an
+// undefined position get the bucket past the table (sorted last, never
+// scanned).
 __global__ void __launch_bounds__(kDedupThreads)
-    k_dedup_insert(const float2* __restrict__ P, int n_cand, int n_ref, int kmid, float inv_cell,
-                   int* __restrict__ head, uint32_t mask, int* __restrict__ next) {
+    k_dedup_items(const float2* __restrict__ P, int n_cand, int n_ref, float inv_cell2, uint32_t mask,
+                  unsigned long long* __restrict__ items) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cand) return;
-  int cx, cy;
-  if (!cell_of(P[(int64_t)i * n_ref + kmid], inv_cell, cx, cy)) return;
-  next[i] = atomicExch(head + cell_hash(cx, cy, mask), i);
+  GridKey g;
+  const uint32_t b = grid_key(P + (int64_t)i * n_ref, n_ref, inv_cell2, g) ? key_hash(g.c, mask) : mask + 1;
+  items[i] = ((unsigned long long)b << 32) | (unsigned)i;
+}
+
+// Runs of the sorted items: first[b] .. last[b] (exclusive) hold bucket b.
+__global__ void __launch_bounds__(kDedupThreads)
+    k_dedup_runs(const unsigned long long* __restrict__ items, int n_cand, uint32_t mask,
+                 int* __restrict__ first, int* __restrict__ last) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_cand) return;
+  const uint32_t b = (uint32_t)(items[i] >> 32);
+  if (b > mask) return;
+  if (i == 0 || (uint32_t)(items[i - 1] >> 32) != b) first[b] = i;
+  if (i == n_cand - 1 || (uint32_t)(items[i + 1] >> 32) != b) last[b] = i + 1;
 }
 
 // keep[i] = 0 when a candidate of smaller rank (index) lies within r of i at
 // every reference exposure (both positions defined), else 1.
 __global__ void __launch_bounds__(kDedupThreads)
-    k_dedup_mark(const float2* __restrict__ P, int n_cand, int n_ref, int kmid, float inv_cell, float r2,
-                 const int* __restrict__ head, uint32_t mask, const int* __restrict__ next,
-                 uint8_t* __restrict__ keep) {
+    k_dedup_mark(const float2* __restrict__ P, int n_cand, int n_ref, float inv_cell2, float r2,
+                 const unsigned long long* __restrict__ items, const int* __restrict__ first,
+                 const int* __restrict__ last, uint32_t mask, uint8_t* __restrict__ keep) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cand) return;
   const float2* pi = P + (int64_t)i * n_ref;
-  int cx, cy;
+  GridKey g;
   bool dup = false;
-  if (cell_of(pi[kmid], inv_cell, cx, cy)) {
-    for (int dy = -1; dy <= 1 && !dup; ++dy) {
-      for (int dx = -1; dx <= 1 && !dup; ++dx) {
-        for (int j = head[cell_hash(cx + dx, cy + dy, mask)]; j >= 0 && !dup; j = next[j]) {
-          if (j >= i) continue;
-          const float2* pj = P + (int64_t)j * n_ref;
-          bool close = true;
-          for (int k = 0; k < n_ref && close; ++k) {
-            const float ex = pi[k].x - pj[k].x, ey = pi[k].y - pj[k].y;
-            close = ex * ex + ey * ey < r2;    // false for NaN
-          }
-          dup = close;
+  if (grid_key(pi, n_ref, inv_cell2, g)) {
+    const int dims = n_ref == 1 ? 2 : 4;       // one reference: its two coordinates only
+    for (int combo = 0; combo < (1 << dims) && !dup; ++combo) {
+      int c[4];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) c[d] = g.c[d] + (((combo >> d) & 1) ? g.side[d] : 0);
+      const uint32_t b = key_hash(c, mask);
+      const int e = last[b];
+      for (int q = first[b]; q < e && !dup; ++q) {
+        const int j = (int)(unsigned)items[q];
+        if (j >= i) break;                     // the run is in rank order
+        const float2* pj = P + (int64_t)j * n_ref;
+        bool close = true;
+        for (int k = 0; k < n_ref && close; ++k) {
+          const float ex = pi[k].x - pj[k].x, ey = pi[k].y - pj[k].y;
+          close = ex * ex + ey * ey < r2;      // false for NaN
         }
+        dup = close;
       }
     }
   }
@@ -224,14 +274,15 @@ __global__ void __launch_bounds__(kScanBlock) k_keep_write(const uint8_t* __rest
 
 size_t dedup_scratch_bytes(int64_t n_cand, int n_ref, uint32_t table) {
   const int64_t nb = (n_cand + kScanBlock - 1) / kScanBlock;
-  // six sub-buffers, each rounded up to 256 bytes by launch_dedup
-  return sizeof(float2) * n_cand * n_ref + sizeof(int) * (table + n_cand) + n_cand +
-         sizeof(int) * (2 * nb + 1) + 6 * 256;
+  // eight sub-buffers, each rounded up to 256 bytes by launch_dedup
+  return sizeof(float2) * n_cand * n_ref + 2 * sizeof(unsigned long long) * n_cand +
+         sort_hist_bytes(n_cand) + 2 * sizeof(int) * (size_t)table + n_cand + sizeof(int) * (2 * nb + 1) +
+         8 * 256;
 }
 
 uint32_t dedup_table_size(int64_t n_cand) {
   uint32_t t = 1024;
-  while ((int64_t)t < 2 * n_cand && t < (1u << 30)) t <<= 1;
+  while ((int64_t)t < 2 * n_cand && t < (1u << 26)) t <<= 1;
   return t;
 }
 
@@ -249,22 +300,32 @@ cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64
     return q;
   };
   float2* P = reinterpret_cast<float2*>(take(sizeof(float2) * n_cand * n_ref));
-  int* head = reinterpret_cast<int*>(take(sizeof(int) * table));
-  int* next = reinterpret_cast<int*>(take(sizeof(int) * n_cand));
+  auto* items_a = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * n_cand));
+  auto* items_b = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * n_cand));
+  unsigned int* hist = reinterpret_cast<unsigned int*>(take(sort_hist_bytes(n_cand)));
+  int* first = reinterpret_cast<int*>(take(sizeof(int) * table));
+  int* last = reinterpret_cast<int*>(take(sizeof(int) * table));
   uint8_t* keep = reinterpret_cast<uint8_t*>(take(n_cand));
   int* counts = reinterpret_cast<int*>(take(sizeof(int) * nb));
   int* offsets = reinterpret_cast<int*>(take(sizeof(int) * (nb + 1)));
   const unsigned grid = (unsigned)((n_cand + kDedupThreads - 1) / kDedupThreads);
-  cudaError_t e = cudaMemsetAsync(head, 0xff, sizeof(int) * table, st);   // -1: empty
+  // empty buckets: first = last = 0
+  cudaError_t e = cudaMemsetAsync(first, 0, sizeof(int) * table, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(last, 0, sizeof(int) * table, st);
   if (e != cudaSuccess) return e;
   k_track_ref<<<grid, kDedupThreads, 0, st>>>(states, n, t0, cand, n_cand, ex, ref_dev, n_ref, ph, P,
                                               counters);
-  const int kmid = n_ref / 2;
-  const float inv_cell = 1.0f / radius;
-  k_dedup_insert<<<grid, kDedupThreads, 0, st>>>(P, (int)n_cand, n_ref, kmid, inv_cell, head, table - 1,
-                                                 next);
-  k_dedup_mark<<<grid, kDedupThreads, 0, st>>>(P, (int)n_cand, n_ref, kmid, inv_cell, radius * radius,
-                                               head, table - 1, next, keep);
+  const float inv_cell2 = 0.5f / radius;       // cells of size 2r
+  const uint32_t mask = table - 1;
+  k_dedup_items<<<grid, kDedupThreads, 0, st>>>(P, (int)n_cand, n_ref, inv_cell2, mask, items_a);
+  int bits = 0;                                // bucket values up to mask + 1 = table
+  while ((1u << bits) <= table) ++bits;
+  unsigned long long* sorted = nullptr;
+  if ((e = sort_items_hi32(items_a, items_b, hist, n_cand, (bits + 7) / 8, &sorted, st)) != cudaSuccess)
+    return e;
+  k_dedup_runs<<<grid, kDedupThreads, 0, st>>>(sorted, (int)n_cand, mask, first, last);
+  k_dedup_mark<<<grid, kDedupThreads, 0, st>>>(P, (int)n_cand, n_ref, inv_cell2, radius * radius, sorted,
+                                               first, last, mask, keep);
   k_keep_count<<<(unsigned)nb, kScanBlock, 0, st>>>(keep, (int)n_cand, counts);
   k_keep_scan<<<1, kScanBlock, 0, st>>>(counts, (int)nb, offsets);
   k_keep_write<<<(unsigned)nb, kScanBlock, 0, st>>>(keep, (int)n_cand, offsets, cand, out);

@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(1024) k_sort_small(const unsigned long long* _
 // tie-break.  Per pass: block histograms (bin-major), one exclusive scan, and
 // a stable scatter that ranks equal digits by position inside each block.
 // ---------------------------------------------------------------------------
-constexpr int kRsItems = 2048;               // items per block (8 rounds of 256)
+constexpr int kRsItems = 8192;               // items per block (32 rounds of 256)
 
 __global__ void __launch_bounds__(kThreads) k_rs_hist(const unsigned long long* __restrict__ in,
                                                       int64_t k, int shift, int nb,
@@ -255,25 +255,37 @@ __global__ void __launch_bounds__(kThreads) k_rs_hist(const unsigned long long* 
   hist[(int64_t)threadIdx.x * nb + blockIdx.x] = h[threadIdx.x];   // bin-major
 }
 
-__global__ void k_rs_scan(unsigned int* hist, int64_t total) {
-  __shared__ unsigned int sc[1024];
+// Exclusive scan of the bin-major block histograms by one block of 1024
+// threads: warp shuffles inside each chunk of 1024, a carry across chunks.
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned int* hist, int64_t total) {
+  __shared__ unsigned int warp_sum[32];
   __shared__ unsigned int carry;
   if (threadIdx.x == 0) carry = 0u;
   __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t base = 0; base < total; base += 1024) {
     const int64_t i = base + threadIdx.x;
     const unsigned int v = i < total ? hist[i] : 0u;
-    sc[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      const unsigned int t = threadIdx.x >= off ? sc[threadIdx.x - off] : 0u;
-      __syncthreads();
-      sc[threadIdx.x] += t;
-      __syncthreads();
+    unsigned int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (i < total) hist[i] = carry + sc[threadIdx.x] - v;
+    if (lane == 31) warp_sum[warp] = x;
     __syncthreads();
-    if (threadIdx.x == 1023) carry += sc[1023];
+    if (warp == 0) {
+      unsigned int w = warp_sum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const unsigned int incl = x + (warp > 0 ? warp_sum[warp - 1] : 0u) + carry;
+    if (i < total) hist[i] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = incl;
     __syncthreads();
   }
 }
@@ -324,6 +336,42 @@ __global__ void k_unpack(const unsigned long long* __restrict__ items, int64_t k
 }
 
 }  // namespace
+
+// Number of orbits whose nu is at least thr (NaN never counts).
+__global__ void __launch_bounds__(kThreads) k_count_ge(const float* __restrict__ nu, int64_t n, float thr,
+                                                       unsigned long long* __restrict__ out) {
+  unsigned int c = 0u;
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads)
+    c += nu[i] >= thr ? 1u : 0u;
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, (unsigned long long)c);
+}
+
+cudaError_t launch_count_ge(const float* nu, int64_t n, float thr, unsigned long long* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int blocks = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, 152 * 8);
+  k_count_ge<<<blocks, kThreads, 0, st>>>(nu, n, thr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t sort_items_hi32(unsigned long long* a, unsigned long long* b, unsigned int* hist, int64_t k,
+                            int passes, unsigned long long** sorted, cudaStream_t st) {
+  const int nb = (int)((k + kRsItems - 1) / kRsItems);
+  for (int pass = 0; pass < passes; ++pass) {
+    const int shift = 32 + 8 * pass;
+    k_rs_hist<<<nb, kThreads, 0, st>>>(a, k, shift, nb, hist);
+    k_rs_scan<<<1, 1024, 0, st>>>(hist, (int64_t)256 * nb);
+    k_rs_scatter<<<nb, kThreads, 0, st>>>(a, b, k, shift, nb, hist);
+    unsigned long long* t = a;
+    a = b;
+    b = t;
+  }
+  *sorted = a;
+  return cudaGetLastError();
+}
+
+size_t sort_hist_bytes(int64_t k) { return (size_t)256 * ((k + kRsItems - 1) / kRsItems) * 4; }
 
 size_t topk_scratch_bytes(int64_t n, int64_t k) {
   const int64_t nblocks = (n + kChunk - 1) / kChunk;

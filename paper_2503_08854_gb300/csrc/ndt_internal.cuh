@@ -678,6 +678,16 @@ cudaError_t launch_predict(const double* states, int64_t n, double t0, const Exp
                            const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph,
                            double* xy, unsigned long long* counters, cudaStream_t st);
 
+// Number of values of nu (n of them) at least thr, into *out (device).
+cudaError_t launch_count_ge(const float* nu, int64_t n, float thr, unsigned long long* out, cudaStream_t st);
+
+// Stable LSD radix sort (k_topk.cu) of k 64-bit items on bits 32 .. 32 + 8
+// passes - 1, ping-ponging between a and b; *sorted is the buffer that holds
+// the result.  hist needs sort_hist_bytes(k).
+cudaError_t sort_items_hi32(unsigned long long* a, unsigned long long* b, unsigned int* hist, int64_t k,
+                            int passes, unsigned long long** sorted, cudaStream_t st);
+size_t sort_hist_bytes(int64_t k);
+
 // duplicate suppression of ranked candidates (k_dedup.cu)
 uint32_t dedup_table_size(int64_t n_cand);
 size_t dedup_scratch_bytes(int64_t n_cand, int n_ref, uint32_t table);

@@ -79,6 +79,7 @@ _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 _lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
 _lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _vp, C.POINTER(_i64)]
+_lib.ndt_count_candidates.argtypes = [_vp, C.c_float, C.POINTER(_i64)]
 _lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
 
@@ -302,6 +303,13 @@ def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
         raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
 
 
+def count_candidates(ctx, min_snr):
+    """ndt_count_candidates: orbits of the last stack with nu >= min_snr."""
+    c = C.c_int64()
+    _check(ctx, _lib.ndt_count_candidates(ctx, float(min_snr), C.byref(c)))
+    return c.value
+
+
 def dedup_candidates(ctx, states_soa, t0, n_orbits, cand_idx, n_cand, keep_idx, radius_px=4.0, n_ref=3):
     """ndt_dedup_candidates: keep_idx[:returned] = the candidates of cand_idx
     (rank order) with no better-ranked candidate within radius_px at every
@@ -334,4 +342,4 @@ def exported_symbols():
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
-            "ndt_measure_fp64_rate", "ndt_dedup_candidates"]
+            "ndt_measure_fp64_rate", "ndt_dedup_candidates", "ndt_count_candidates"]

@@ -157,3 +157,87 @@ def _stamps(ctx, states, t0, device):
     ndt.trim_candidates(ctx, st, t0, n, cand, trimmed)
     return (bf, f32[:, 0, 10, 10].cpu().numpy().astype(np.float64),
             trimmed.cpu().numpy().astype(np.float64))
+
+
+def track_rms(ctx, sky, cand, device, chunk=65536):
+    """RMS pixel distance (n,) between each candidate's predicted track and
+    its family's injected asteroid (family = index // fam_size) over the
+    exposures where the asteroid's position lies on the chip, from the
+    library's own positions (ndt_predict_positions)."""
+    import torch
+    fam = sky.meta["fam_size"]
+    n_exp = sky.ex.n
+    W, H = float(sky.ex.width[0]), float(sky.ex.height[0])
+    true_xy = _predict(ctx, sky.inj_states, sky.t0, n_exp, device)
+    cover = ((true_xy[..., 0] >= -0.5) & (true_xy[..., 0] < W - 0.5) &
+             (true_xy[..., 1] >= -0.5) & (true_xy[..., 1] < H - 0.5))
+    cand = np.asarray(cand, np.int64)
+    out = np.empty(len(cand))
+    for s in range(0, len(cand), chunk):
+        c = cand[s:s + chunk]
+        f = torch.as_tensor(c // fam, device=device)
+        xy = _predict(ctx, sky.states[c], sky.t0, n_exp, device)
+        d2 = ((xy - true_xy[f]) ** 2).sum(-1)
+        cv = cover[f]
+        rms = torch.sqrt(torch.where(cv, d2, torch.zeros_like(d2)).sum(1) / cv.sum(1).clamp(min=1))
+        out[s:s + chunk] = rms.cpu().numpy()
+    return out
+
+
+def fpr_at_object_recall(score, match, obj, n_obj, recall):
+    """Threshold and false-positive rate of a score on a candidate list: the
+    highest threshold at which ``recall`` of the n_obj injected objects have a
+    matching entry (match, obj: its object) scoring at least the threshold;
+    the FPR is the fraction of non-matching entries at or above it."""
+    score = np.asarray(score, np.float64)
+    best = np.full(n_obj, -np.inf)
+    np.maximum.at(best, np.asarray(obj)[match], score[match])
+    k = int(math.ceil(recall * n_obj))
+    thr = float(np.sort(best)[::-1][k - 1])
+    neg = score[~match]
+    return (float(np.mean(neg >= thr)) if len(neg) else None), thr
+
+
+def make_survey_set(ctx, seed, device, *, n_true=1000, fam_size=512, snr_range=(0.3, 3.0), nu_min=5.0,
+                    match_px=2.0, max_pos_per_obj=32, size=4096, n_exp=200):
+    """Stamps from an MBA-like survey: the cadence, chips, PSF and noise of
+    the MBA workload, with candidate families (each asteroid's true state and
+    jittered neighbours).  Positives: orbits with nu >= nu_min whose track
+    stays within match_px RMS of their asteroid's (at most max_pos_per_obj
+    per asteroid, drawn at random); negatives: as many orbits with nu >=
+    nu_min that do not, i.e. tracks that share only part of an asteroid's
+    path, and noise peaks.  Returns (stamps_bf16, labels, kind: 0 positive,
+    4 negative, nu)."""
+    import torch
+    sky = synth.mba_sky(n_exp=n_exp, size=size, n_true=n_true, fam_size=fam_size, seed=seed,
+                        snr_range=snr_range, scale_arcsec=10.5 * 4096 / size)
+    imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
+    torch.cuda.synchronize(device)
+    ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype="f32")
+    pos = _predict(ctx, sky.inj_states, sky.t0, sky.ex.n, device)
+    synth.render_sources_torch(imgs, pos, sky.inj_flux, sky.ex.sigma)
+    torch.cuda.synchronize(device)
+    ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype="bf16")
+    del imgs
+    n = len(sky.states)
+    st = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(device)
+    nu = torch.empty(n, device=device)
+    torch.cuda.synchronize(device)
+    ndt.stack_orbits(ctx, st, sky.t0, n, snr=nu)
+    nu = nu.cpu().numpy()
+    cand = np.flatnonzero(nu >= nu_min)
+    match = track_rms(ctx, sky, cand, device) < match_px
+    rng = np.random.default_rng(seed + 17)
+    pos_idx = []
+    obj = cand // fam_size
+    for o in np.unique(obj[match]):
+        m = cand[match & (obj == o)]
+        pos_idx.append(rng.choice(m, min(len(m), max_pos_per_obj), replace=False))
+    pos_idx = np.concatenate(pos_idx) if pos_idx else np.zeros(0, np.int64)
+    negs = cand[~match]
+    neg_idx = rng.choice(negs, min(len(negs), len(pos_idx)), replace=False)
+    sel = np.concatenate([pos_idx, neg_idx])
+    kind = np.concatenate([np.zeros(len(pos_idx)), np.full(len(neg_idx), 4)]).astype(np.int64)
+    x, c0, _ = _stamps(ctx, sky.states[sel], sky.t0, device)
+    y = torch.as_tensor((kind == 0).astype(np.float32), device=device)
+    return x, y, kind, nu[sel]

@@ -75,3 +75,29 @@ def test_dedup_host_pointers_and_edges(gpu):
         ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), one, 2, o2, radius_px=0.0)
     with pytest.raises(ndt.NdtError):
         ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), one, 2, o2, n_ref=9)
+
+
+def test_count_candidates_matches_oracle_nu(gpu):
+    """ndt_count_candidates against the oracle's stacked statistic: the
+    number of orbits at or above each threshold, skipping thresholds that
+    fall within the SNR tolerance of an oracle value."""
+    import oracle as O
+    sky = synth.grid_sky(n_exp=6, size=100, n_r=4, n_v=32, scale_arcsec=1.0, inj_snr=4.0, n_inj=3,
+                         seed=3)
+    imgs = synth.noise_images(sky.ex, sky.seed)
+    synth.render_sources(imgs, O.predict(sky.inj_states, sky.t0, sky.ex), sky.inj_flux, sky.ex.sigma)
+    gpu.load(sky.ex, imgs)
+    n = len(sky.states)
+    ndt.stack_orbits(gpu.ctx, gpu.soa(sky.states), sky.t0, n)
+    ref = O.stack(sky.states, sky.t0, sky.ex, images=list(imgs))
+    nu = O.snr(ref["Psi"], ref["Phi"], ref["nobs"])
+    fin = nu[np.isfinite(nu)]
+    checked = 0
+    for thr in (-1.0, 0.0, 1.5, 3.0, 5.0, 1e9):
+        if np.any(np.abs(fin - thr) <= 1e-5 * np.maximum(1.0, np.abs(fin))) or np.any(ref["n_amb"] > 0):
+            continue
+        assert ndt.count_candidates(gpu.ctx, thr) == int(np.sum(nu >= thr)), thr
+        checked += 1
+    assert checked >= 4
+    with pytest.raises(ndt.NdtError):
+        ndt.count_candidates(gpu.ctx, float("nan"))
