@@ -65,8 +65,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["mba", "batched"], default="mba",
-                   help="mba: the MBA-scale survey (default); batched: uneven orbit families")
+    p.add_argument("--workload", choices=["mba", "batched", "sparse"], default="mba",
+                   help="mba: the MBA-scale survey (default); batched: uneven orbit families; "
+                        "sparse: 20,000 small exposures, each orbit on well under 1 % of them")
     p.add_argument("--n-fam", type=int, default=4096, help="families of the batched workload")
     p.add_argument("--fam-size", type=int, default=16384, help="orbits per family")
     p.add_argument("--n-true", type=int, default=1000)
@@ -83,6 +84,8 @@ def parse():
     p.add_argument("--no-noise", action="store_true", help="skip the iterative-MAD noise timing")
     p.add_argument("--no-batched", action="store_true",
                    help="skip the batched uneven workload's sub-record (MBA runs only)")
+    p.add_argument("--no-sparse", action="store_true",
+                   help="skip the sparse-regime sub-record (MBA runs only)")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
     p.add_argument("--vet-survey-stamps", type=int, default=200_000,
                    help="MBA-like survey stamps in the vetting network's training set")
@@ -166,6 +169,27 @@ def make_workload(args, rank, device):
         states = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(device)
         torch.cuda.synchronize(device)
         return sky, stream, imgs, states
+    if args.workload == "sparse":
+        sky = synth.sparse_sky(seed=7 + rank)
+        sky.fam_dev = None
+        imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
+        ctx = ndt.create(device.index, stream)
+        try:
+            ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype="f32")
+            st = torch.from_numpy(np.ascontiguousarray(sky.inj_states.T)).to(device)
+            xy = torch.empty(len(sky.inj_states) * sky.ex.n * 2, dtype=torch.float64, device=device)
+            torch.cuda.synchronize(device)
+            ndt.predict_positions(ctx, st, sky.t0, len(sky.inj_states), xy)
+        finally:
+            ndt.destroy(ctx)
+        xy = xy.view(len(sky.inj_states), sky.ex.n, 2)
+        W = float(sky.ex.width[0])
+        far = (xy[..., 0] < -20) | (xy[..., 0] > W + 20) | (xy[..., 1] < -20) | (xy[..., 1] > W + 20)
+        xy[far] = float("nan")                 # render only where a source is near the chip
+        synth.render_sources_torch(imgs, xy, sky.inj_flux, sky.ex.sigma)
+        states = torch.from_numpy(np.ascontiguousarray(sky.states.T)).to(device)
+        torch.cuda.synchronize(device)
+        return sky, stream, imgs, states
     sky = synth.mba_sky(n_exp=args.n_exp, size=args.size, n_true=args.n_true,
                         fam_size=args.fam_size, seed=2 + rank,
                         scale_arcsec=10.5 * 4096 / args.size)
@@ -190,8 +214,8 @@ def make_workload(args, rank, device):
 
 
 class Form:
-    def __init__(self, name, plane, mode, graph):
-        self.name, self.plane, self.mode, self.graph = name, plane, mode, graph
+    def __init__(self, name, plane, mode, graph, block=True):
+        self.name, self.plane, self.mode, self.graph, self.block = name, plane, mode, graph, block
 
 
 NU_MIN = 5.0        # detection threshold of the candidate list (stacked SNR)
@@ -361,6 +385,7 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
                 tiles = {"orbit_tile": ot, "exp_tile": et,
                          "sweep_ms": [round(float(t), 2) for t in times]}
             ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, ot, et, use_graph=form.graph)
+        ndt.set_block_test(ctx, form.block)
         cand = Candidates(n, device, vet_params if form.name == "chosen" else None)
         run_steps(ctx, stream, sky, imgs, states, args.warmup, form.plane, cand)
         launches0 = ndt.get_stats(ctx)["kernel_launches"]
@@ -383,6 +408,7 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
         out = dict(step_ms=step_ms, stack_ms=stack_ms, cand_ms=cand_ms,
                    wall_s=wall, launches=launches, skipped=stats["offchip_skipped"],
                    valid=stats["valid_samples"], samples=stats["samples"], quality=quality,
+                   blocked=stats["block_skipped"],
                    planes_ms=stats["last_planes_ms"], topk_ms=stats["last_topk_ms"], tiles=tiles)
         if cand.vet_params is not None and args.vet_batch > 0:
             out["vet_batch"] = vet_batch_rate(args, ctx, stream, sky, states, vet_params, device)
@@ -674,6 +700,9 @@ def form_record(res):
             "candidates_per_s": q["list"] / s, "candidates": q,
             "valid_fraction": res["valid"] / max(res["samples"], 1),
             "offchip_skipped_fraction": res["skipped"] / max(res["samples"], 1),
+            "block_skipped_fraction": res["blocked"] / max(res["samples"], 1),
+            "fp64_step_fraction": (res["samples"] - res["skipped"]) / max(res["samples"], 1),
+            "pairs_rejected_per_s": res["skipped"] / s,
             "tiles": res["tiles"]}
 
 
@@ -714,6 +743,38 @@ def batched_subrecord(args, rank, device, barrier, world, max_over_ranks, rates)
     out["value"] = r["samples"] * world / max_over_ranks(statistics.mean(r["step_ms"]) / 1e3)
     out["unit"] = UNIT
     out["roofline"] = stack_roofline("batched", b.plane, r, rates)
+    del imgs, states
+    torch.cuda.empty_cache()
+    return out
+
+
+def sparse_subrecord(args, rank, device, barrier, world, max_over_ranks, vet_params):
+    """The sparse regime (20,000 exposures of 512^2 over a year, 1M orbits,
+    each orbit on well under 1 % of the exposures) measured in the same run:
+    the chosen form with and without the block cone test, and the plain
+    form; fewer steps than the headline."""
+    import copy
+    import torch
+    b = copy.copy(args)
+    b.workload, b.no_vet = "sparse", vet_params is None
+    b.steps, b.warmup, b.tiles = min(args.steps, 3), 3, "128,16"
+    b.no_e2e, b.vet_batch = True, 0
+    sky, stream, imgs, states = make_workload(b, rank, device)
+    forms = [Form("chosen", b.plane, "persistent", True, block=True),
+             Form("chosen_without_block_test", b.plane, "persistent", True, block=False),
+             Form("plain", "f32", "plain", False)]
+    n = states.shape[1]
+    out = {"workload": (f"sparse survey: {sky.ex.n} exposures {int(sky.ex.width[0])}^2 over a year, "
+                        f"{n} orbits ({sky.meta['n_fam']} families), {len(sky.inj_states)} injected, "
+                        f"all orbits x all exposures"),
+           "steps": b.steps, "warmup": b.warmup, "tiles": b.tiles}
+    for f in forms:
+        r, _ = bench_form(b, f, sky, stream, imgs, states, device, barrier,
+                          vet_params if f.name == "chosen" else None)
+        out[f.name] = form_record(r)
+    r = out["chosen"]
+    out["value"] = r["samples_per_s"] * world
+    out["unit"] = UNIT
     del imgs, states
     torch.cuda.empty_cache()
     return out
@@ -811,6 +872,9 @@ def main():
         torch.cuda.empty_cache()
         line["batched"] = batched_subrecord(args, rank, device, barrier, world, max_over_ranks,
                                             rates)
+    if args.workload == "mba" and not args.no_sparse:
+        torch.cuda.empty_cache()
+        line["sparse"] = sparse_subrecord(args, rank, device, barrier, world, max_over_ranks, vet_params)
     line["clocks"] = clocks.stop()
     if host is not None:
         rate, cores, desc = cpu_oracle_rate(sky, host, args.cpu_seconds)

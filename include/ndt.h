@@ -100,6 +100,7 @@ typedef struct {
   int32_t plane_dtype;
   int64_t offchip_skipped;   /* samples of the last stack whose FP64 work the
                                 off-chip test removed (persistent form)     */
+  int64_t block_skipped;     /* of which the block cone test removed         */
 } ndt_stats;
 
 typedef struct ndt_ctx ndt_ctx;
@@ -231,6 +232,22 @@ ndt_status ndt_set_filter_broadening(ndt_ctx *ctx, float sigma_px);
    chained state differs.  No counterpart in the paper: its Algorithm 1
    propagates every (orbit, image) pair.  enabled = 0 switches it off. */
 ndt_status ndt_set_offchip_test(ndt_ctx *ctx, int32_t enabled);
+
+/* Block cone test of the persistent form (on by default; it acts only with
+   the off-chip test on).  For every staged block of exposures (the
+   exp_tile records a team walks at a time, in epoch order) each warp bounds
+   the sky directions its orbits can take during the block by one cone: each
+   orbit's direction at the block's middle epoch, predicted in FP32 from its
+   last FP64 state, widened by the rigorous error bound of the off-chip test,
+   the motion over the block and the spread of the block's observer
+   positions.  Exposures whose chip cone (tangent point, largest off-axis
+   angle + 0.01 rad) lies outside the warp's cone are skipped by the whole
+   warp at a few FP32 instructions each instead of one off-chip test per
+   orbit and exposure: the sky index of the sparse regime, where each orbit
+   meets a small fraction of many exposures (paper sec. 3: every (image,
+   orbit) pair is checked by brute force there).  The stacked sums are those
+   of the full computation.  enabled = 0 switches it off. */
+ndt_status ndt_set_block_test(ndt_ctx *ctx, int32_t enabled);
 
 /*
  * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}

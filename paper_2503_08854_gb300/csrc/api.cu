@@ -85,6 +85,7 @@ struct ndt_ctx {
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   int32_t offchip = 1;     // off-chip test of the persistent form
+  int32_t block_test = 1;  // warp cone test per exposure block (persistent form)
   float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
@@ -220,6 +221,9 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
   }
   const double th = std::atan(rmax) + 0.01;
   e.cos_far = th < 0.5 * kPi ? (float)(std::cos(th) * (1.0 - 1e-6)) : -2.0f;
+  // the chip cone of the block test: radius th (the corner angle + 0.01 rad)
+  e.chip_cos = (float)std::cos(std::min(th, kPi));
+  e.chip_sin = (float)std::sin(std::min(th, kPi));
 }
 
 // The power of two nearest to x > 0 (in log2), within the normal FP32 range.
@@ -682,7 +686,7 @@ ndt_status prepare_families(ndt_ctx* ctx, int64_t n, const int64_t* fo_in, const
 ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
   if (ctx->mode == NDT_LAUNCH_PLAIN) {
     NDT_CK(cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream), "memset");
-    NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 8, ctx->stream), "memset");
+    NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 16, ctx->stream), "memset");
     record(ctx, 2);
     NDT_CK(launch_stack_plain(a, ctx->stream), "stack kernel");
     record(ctx, 3);
@@ -694,7 +698,7 @@ ndt_status run_stack(ndt_ctx* ctx, StackArgs& a) {
   auto enqueue = [&]() -> cudaError_t {
     cudaError_t e = cudaMemsetAsync(ctx->queue_head.p, 0, 8, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.p, 0, 16, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 8, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 3, 0, 16, ctx->stream);
     if (e == cudaSuccess) e = launch_stack_persistent(a, ctx->n_sms, ctx->stream);
     return e;
   };
@@ -781,6 +785,7 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   a.ph = ctx->ph;
   a.t_ref = ctx->t_ref;
   a.offchip_test = persistent ? ctx->offchip : 0;
+  a.block_test = persistent && ctx->offchip ? ctx->block_test : 0;
   s = run_stack(ctx, a);
   if (s != NDT_OK) return s;
   ctx->last_n = n_orbits;
@@ -923,6 +928,12 @@ ndt_status ndt_set_filter_broadening(ndt_ctx* ctx, float sigma_px) {
 ndt_status ndt_set_offchip_test(ndt_ctx* ctx, int32_t enabled) {
   if (!ctx) return NDT_EINVAL;
   ctx->offchip = enabled ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_set_block_test(ndt_ctx* ctx, int32_t enabled) {
+  if (!ctx) return NDT_EINVAL;
+  ctx->block_test = enabled ? 1 : 0;
   return NDT_OK;
 }
 
@@ -1323,10 +1334,11 @@ ndt_status ndt_get_stats(ndt_ctx* ctx, ndt_stats* out) {
   NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
   std::memset(out, 0, sizeof *out);
-  unsigned long long cnt[4];
-  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 32, cudaMemcpyDeviceToHost), "counters");
+  unsigned long long cnt[5];
+  NDT_CK(cudaMemcpy(cnt, ctx->counters.p, 40, cudaMemcpyDeviceToHost), "counters");
   out->kernel_launches = ctx->launches;
   out->offchip_skipped = (int64_t)cnt[3];
+  out->block_skipped = (int64_t)cnt[4];
   out->samples = ctx->samples;
   out->valid_samples = (int64_t)cnt[0];
   out->kepler_failures = (int64_t)cnt[1];

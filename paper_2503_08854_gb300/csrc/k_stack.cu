@@ -52,6 +52,7 @@ struct Walk {
   CSum sp, sf;
   int cnt;
   int skipped;         // samples whose FP64 work the off-chip test removed
+  int blocked;         // of which the block cone test removed
   bool failed;
   float rf[3], vf[3], tf;   // FP32 copy of the state and its epoch (off-chip test)
 };
@@ -76,6 +77,7 @@ __device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double*
   w.sf = CSum{0.0f, 0.0f};
   w.cnt = 0;
   w.skipped = 0;
+  w.blocked = 0;
   w.failed = false;
   walk_fp32_copy(w, (float)(t0 - t_ref));
 }
@@ -89,6 +91,59 @@ __device__ __forceinline__ bool warp_skips(Walk& w, const Phys& ph, const ExpDev
   if (!__all_sync(0xffffffffu, off)) return false;
   if (active && !w.failed) w.skipped += 1;
   return true;
+}
+
+// Block cone test: the exposures of a staged block (cnt <= 32 records, epoch
+// order) that the warp's orbits cannot reach.  Each lane bounds its orbit's
+// direction over the block by a cone (block_direction); the warp's cone has
+// the first working lane's direction as centre and as radius the largest
+// chord angle (2 asin(chord/2) <= 1.05 chord for chord <= 0.5) plus that
+// lane's bound.  Exposure jj is unreachable when the angle between the
+// warp's centre and its tangent point exceeds the warp radius plus the chip
+// cone's radius; lane jj tests exposure jj and a ballot gives the mask.
+// Warp-uniform; every lane must call it.
+__device__ __forceinline__ unsigned warp_block_mask(const Walk& w, const Phys& ph, const ExpDev* blk, int cnt,
+                                                    bool active) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned all = cnt >= 32 ? full : ((1u << cnt) - 1u);
+  const ExpDev& em = blk[cnt >> 1];
+  const float tm = em.tf;
+  const float h = fmaxf(fabsf(blk[0].tf - tm), fabsf(blk[cnt - 1].tf - tm));
+  const float om[3] = {em.obs_f[0], em.obs_f[1], em.obs_f[2]};
+  float d = 0.0f;
+  if (lane < cnt) {
+    const float dx = blk[lane].obs_f[0] - om[0], dy = blk[lane].obs_f[1] - om[1], dz = blk[lane].obs_f[2] - om[2];
+    d = sqrtf(dx * dx + dy * dy + dz * dz) * 1.0001f + 1e-7f;
+  }
+  for (int o = 16; o > 0; o >>= 1) d = fmaxf(d, __shfl_xor_sync(full, d, o));
+  const bool has = active && !w.failed;
+  const unsigned act = __ballot_sync(full, has);
+  if (act == 0u) return all;                   // no orbit of this warp needs any sample
+  float u[3] = {0.0f, 0.0f, 0.0f}, ang = 0.0f;
+  if (has) ang = block_direction(ph, w.oc, w.rf, w.vf, w.tf, tm, h, om, d, u);
+  const int lead = __ffs(act) - 1;
+  const float c[3] = {__shfl_sync(full, u[0], lead), __shfl_sync(full, u[1], lead),
+                      __shfl_sync(full, u[2], lead)};
+  float th = 0.0f;
+  if (has) {
+    const float ex = u[0] - c[0], ey = u[1] - c[1], ez = u[2] - c[2];
+    const float chord = sqrtf(ex * ex + ey * ey + ez * ez);
+    th = chord <= 0.5f ? fmaf(1.05f, chord, 1e-6f) + ang : INFINITY;
+    if (!(th >= 0.0f)) th = INFINITY;          // NaN
+  }
+  for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(full, th, o));
+  if (!(th < 1.0f)) return 0u;
+  float sr, cr;
+  sincosf(th, &sr, &cr);
+  bool miss = false;
+  if (lane < cnt) {
+    const ExpDev& e = blk[lane];
+    const float cd = c[0] * e.p0_f[0] + c[1] * e.p0_f[1] + c[2] * e.p0_f[2];
+    // cos(th + R) = cos th cos R - sin th sin R, with th + R < 2.5 < pi
+    miss = e.chip_cos > 0.0707f && cd < fmaf(cr, e.chip_cos, -sr * e.chip_sin) - 1e-6f;
+  }
+  return __ballot_sync(full, miss) & all;
 }
 
 template <int PT, bool FP32_COPY = false>
@@ -115,7 +170,7 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
 
 __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, int64_t o,
                                             bool active) {
-  int valid = 0, fails = 0, skipped = 0;
+  int valid = 0, fails = 0, skipped = 0, blocked = 0;
   if (active) {
     const float P = w.sp.value(), F = w.sf.value();
     if (a.psi_sum) a.psi_sum[o] = P;
@@ -128,16 +183,19 @@ __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, i
     valid = w.cnt;
     fails = w.failed ? 1 : 0;
     skipped = w.skipped;
+    blocked = w.blocked;
   }
   for (int off = 16; off > 0; off >>= 1) {
     valid += __shfl_xor_sync(0xffffffffu, valid, off);
     fails += __shfl_xor_sync(0xffffffffu, fails, off);
     skipped += __shfl_xor_sync(0xffffffffu, skipped, off);
+    blocked += __shfl_xor_sync(0xffffffffu, blocked, off);
   }
   if ((threadIdx.x & 31) == 0 && a.counters) {
     if (valid) atomicAdd(a.counters + 0, (unsigned long long)valid);
     if (fails) atomicAdd(a.counters + 1, (unsigned long long)fails);
     if (skipped) atomicAdd(a.counters + 3, (unsigned long long)skipped);
+    if (blocked) atomicAdd(a.counters + 4, (unsigned long long)blocked);
   }
 }
 
@@ -222,9 +280,18 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
         dst[i] = __ldg(reinterpret_cast<const double*>(a.ex + j) + wd);
       }
       team_sync<TEAM>(team);
+      // exposures of the block that no orbit of this warp can reach
+      const unsigned miss = a.block_test ? warp_block_mask(w, a.ph, stage[team], cnt, active) : 0u;
       // every lane runs the loop: the off-chip vote is warp-wide
       for (int jj = 0; jj < cnt; ++jj) {
         const ExpDev& e = stage[team][jj];
+        if ((miss >> jj) & 1u) {
+          if (active && !w.failed) {
+            w.skipped += 1;
+            w.blocked += 1;
+          }
+          continue;
+        }
         if (a.offchip_test && warp_skips(w, a.ph, e, active)) continue;
         walk_sample<PT, true>(w, a.ph, e, a.planes);
       }

@@ -38,7 +38,7 @@ struct ExpDev {
   int32_t tiles_x;   // ceil(W / 32)
   float s_psi;       // dequantisation scale of psi (1 for FP32 planes)
   float s_phi;       // dequantisation scale of phi
-  int32_t pad_;
+  float chip_cos;    // cos of the chip cone's radius (largest off-axis angle + 0.01 rad)
   // FP32 copies for the off-chip test of the persistent form
   float tf;          // epoch - t_ref (days), t_ref = earliest exposure epoch
   float obs_f[3], p0_f[3], ax_f[3], ay_f[3], crpix_f[2];
@@ -48,7 +48,7 @@ struct ExpDev {
   // crpix_h as a high/low pair: the double-float projection of the stack
   float p0_l[3], ax_l[3], ay_l[3], crh_h[2], crh_l[2];
   float obs_l[3];    // low parts of obs (high parts: obs_f), for the double-float light time
-  float pad3_;
+  float chip_sin;    // sin of the chip cone's radius
 };
 static_assert(sizeof(ExpDev) == 288 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
@@ -580,6 +580,40 @@ __device__ __forceinline__ bool certainly_off_chip(const Phys& ph, const OrbitCo
   return x < -0.5f - m || x > (float)e.W - 0.5f + m || y < -0.5f - m || y > (float)e.H - 0.5f + m;
 }
 
+// Block cone test of the persistent form (FP32).  For a block of exposures
+// (epochs within h of the middle one, observers within d_obs of its
+// observer), each lane predicts its orbit's position at the middle epoch tm
+// from its last FP64 state, as in certainly_off_chip, and bounds the angle
+// between that direction from the middle observer and the true direction of
+// any sample of the block: the Taylor remainder jerk6 |dt|^3 and the FP32
+// slack of certainly_off_chip, the motion over the block (v_q h), the
+// observer offset d_obs, light time (|rho| v_q / c plus its acceleration
+// term).  Returns the unit direction u and that angular radius (INFINITY
+// when the bound is unusable).
+__device__ __forceinline__ float block_direction(const Phys& ph, const OrbitConst& oc, const float rf[3],
+                                                 const float vf[3], float tf, float tm, float h,
+                                                 const float obs_mid[3], float d_obs, float u[3]) {
+  const float dt = tm - tf;
+  const float r2 = rf[0] * rf[0] + rf[1] * rf[1] + rf[2] * rf[2];
+  const float ir = rsqrtf(r2);
+  const float k = -ph.gm_f * ir * ir * ir;
+  float rho[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rho[i] = fmaf(0.5f * k * rf[i], dt * dt, fmaf(vf[i], dt, rf[i])) - obs_mid[i];
+  const float rr2 = rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2];
+  const float rr = rr2 * rsqrtf(rr2);
+  const float tau = fmaf(rr, 1.01f, 1e-3f) * ph.inv_c;   // covers |rho| of every sample
+  const float adt = fabsf(dt) + h;
+  const float err = oc.jerk6 * adt * adt * adt + oc.half_acc * tau * tau + 1e-6f * (r2 * ir + rr) +
+                    oc.vq * fmaf(1e-6f, adt, 1e-4f) + oc.vq * (h + tau) + d_obs;
+  const float inv = __frcp_rn(rr);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) u[i] = rho[i] * inv;
+  if (!(rr > 2.0f * err)) return INFINITY;
+  // arcsin(err / (rr - err)) <= 1.6 err / (rr - err) for err / (rr - err) <= 1
+  return 1.6f * __fdividef(err, rr - err);
+}
+
 template <int PT>
 __device__ __forceinline__ float2 gather_plane(const void* __restrict__ planes, const ExpDev& e,
                                                int ix, int iy) {
@@ -666,10 +700,12 @@ struct StackArgs {
   int32_t* nobs;
   float* snr;
   int32_t min_obs;
-  unsigned long long* counters;  // [0] valid samples, [1] Kepler failures, [3] skipped warp-samples
+  unsigned long long* counters;  // [0] valid samples, [1] Kepler failures, [3] skipped samples,
+                                 // [4] of which the block test skipped
   Phys ph;
   double t_ref;                // epoch origin of ExpDev::tf
   int32_t offchip_test;        // persistent form: skip FP64 work of certainly off-chip samples
+  int32_t block_test;          // persistent form: warp cone test per staged exposure block
 };
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);

@@ -40,7 +40,7 @@ class Stats(C.Structure):
                 ("last_stack_ms", C.c_float), ("last_planes_ms", C.c_float),
                 ("last_topk_ms", C.c_float), ("orbit_tile", C.c_int32), ("exp_tile", C.c_int32),
                 ("launch_mode", C.c_int32), ("plane_dtype", C.c_int32),
-                ("offchip_skipped", C.c_int64)]
+                ("offchip_skipped", C.c_int64), ("block_skipped", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -79,6 +79,7 @@ _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 _lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
 _lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _vp, C.POINTER(_i64)]
+_lib.ndt_set_block_test.argtypes = [_vp, _i32]
 _lib.ndt_count_candidates.argtypes = [_vp, C.c_float, C.POINTER(_i64)]
 _lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
@@ -303,6 +304,12 @@ def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
         raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
 
 
+def set_block_test(ctx, enabled=True):
+    """ndt_set_block_test: the persistent form's per-warp cone test of each
+    staged exposure block."""
+    _check(ctx, _lib.ndt_set_block_test(ctx, 1 if enabled else 0))
+
+
 def count_candidates(ctx, min_snr):
     """ndt_count_candidates: orbits of the last stack with nu >= min_snr."""
     c = C.c_int64()
@@ -342,4 +349,5 @@ def exported_symbols():
             "ndt_get_stats", "ndt_synchronize", "ndt_stamps", "ndt_cnn_param_count",
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
-            "ndt_measure_fp64_rate", "ndt_dedup_candidates", "ndt_count_candidates"]
+            "ndt_measure_fp64_rate", "ndt_dedup_candidates", "ndt_count_candidates",
+            "ndt_set_block_test"]

@@ -437,3 +437,63 @@ def batched_sky(*, n_fam=4096, fam_size=16384, n_exp=400, size=2048, days=365.0,
     return Sky(name="batched", ex=ex, t0=t0, states=states, inj_states=seeds,
                inj_flux=np.zeros(n_fam), inj_orbit=fo[:-1].copy(), seed=seed,
                families=(fo, fe, fi), meta=dict(kind=kind, fam_size=fam_size))
+
+
+# --------------------------------------------------------------------------
+# Sparse regime (each orbit meets a small fraction of many small exposures)
+# --------------------------------------------------------------------------
+
+def sparse_sky(*, n_exp=20000, days=365.0, fields=14, visits=4, size=512, scale_arcsec=10.0, n_fam=256,
+               fam_size=4096, n_inj=64, inj_snr=(2.0, 4.0), seed=7, lon=1.2, field_lon=0.12,
+               field_lat=0.06, inc_max_deg=4.0) -> Sky:
+    """The paper's sparse regime: a year of small exposures (``size``^2 px at
+    ``scale_arcsec``).  Each night ``fields`` random fields within
+    +-field_lon rad of the anti-solar ecliptic longitude and +-field_lat rad
+    of the ecliptic are each visited ``visits`` times 25 minutes apart.
+    Candidate orbits: ``n_fam`` families of main-belt hypotheses (a in
+    [2.1, 3.3] AU, e < 0.2, i < inc_max_deg) near opposition at the mid-year
+    epoch t0, each its seed state plus ``fam_size - 1`` jittered neighbours;
+    the seeds of the first ``n_inj`` families are injected with per-image SNR
+    ~ U(inj_snr).  An orbit crosses the chips of well under one percent of the
+    exposures."""
+    rng = np.random.default_rng(seed)
+    per_night = fields * visits
+    nights = int(math.ceil(n_exp / per_night))
+    night = np.repeat(np.arange(nights, dtype=np.float64), per_night)[:n_exp]
+    k = np.tile(np.arange(per_night), nights)[:n_exp]
+    field, visit = k % fields, k // fields
+    mjd = 60000.2 + night * (days / nights) + (field * 1.5 + visit * 25.0) / 1440.0
+    t0 = float(60000.0 + days / 2.0)
+    obs = observer_position(mjd, t0, lon)
+    theta = lon + GAUSS_K * (night * (days / nights) + 60000.2 - t0)   # anti-solar longitude per night
+    off_l = rng.uniform(-field_lon, field_lon, (nights, fields))
+    off_b = rng.uniform(-field_lat, field_lat, (nights, fields))
+    ni = night.astype(np.int64)
+    lam = theta + off_l[ni, field]
+    beta = off_b[ni, field]
+    vec = np.stack([np.cos(beta) * np.cos(lam), np.cos(beta) * np.sin(lam), np.sin(beta)], -1)
+    crval = ecliptic_to_radec_deg(vec)
+    s = scale_arcsec / 3600.0
+    sigma = rng.uniform(1.2, 2.0, n_exp).astype(np.float32).astype(np.float64)
+    ex = Exposures(mjd=mjd, obs=obs, crval=crval,
+                   crpix=np.tile(np.array([size / 2.0, size / 2.0]), (n_exp, 1)),
+                   cd=np.tile(np.array([[-s, 0.0], [0.0, s]]), (n_exp, 1, 1)), sigma=sigma,
+                   var=np.ones(n_exp), width=np.full(n_exp, size, np.int32),
+                   height=np.full(n_exp, size, np.int32))
+    a = rng.uniform(2.1, 3.3, n_fam)
+    e = rng.uniform(0.0, 0.2, n_fam)
+    inc = np.radians(rng.uniform(0.0, inc_max_deg, n_fam))
+    u = rng.uniform(-0.05, 0.05, n_fam)
+    u = np.where(rng.random(n_fam) < 0.5, u, u + math.pi)
+    lam0 = lon + rng.uniform(-0.1, 0.1, n_fam)
+    node = lam0 - np.arctan2(np.cos(inc) * np.sin(u), np.cos(u))
+    argp = rng.uniform(0.0, 2 * math.pi, n_fam)
+    seeds = state_from_elements(a, e, inc, node, argp, u - argp)
+    states = np.repeat(seeds, fam_size, axis=0)
+    jit = np.concatenate([rng.normal(0.0, 3e-4, (len(states), 3)), rng.normal(0.0, 1e-5, (len(states), 3))], 1)
+    jit[::fam_size] = 0.0
+    states += jit
+    snr = rng.uniform(*inj_snr, n_inj)
+    return Sky(name="sparse", ex=ex, t0=t0, states=states, inj_states=seeds[:n_inj].copy(),
+               inj_flux=flux_for_snr(snr, 1.6, 1.0), inj_orbit=np.arange(n_inj, dtype=np.int64) * fam_size,
+               seed=seed, meta=dict(fam_size=fam_size, n_fam=n_fam, inj_snr=snr, size=size))

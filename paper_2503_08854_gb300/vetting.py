@@ -163,7 +163,8 @@ def track_rms(ctx, sky, cand, device, chunk=65536):
     """RMS pixel distance (n,) between each candidate's predicted track and
     its family's injected asteroid (family = index // fam_size) over the
     exposures where the asteroid's position lies on the chip, from the
-    library's own positions (ndt_predict_positions)."""
+    library's own positions (ndt_predict_positions); infinite for families
+    without an injected asteroid."""
     import torch
     fam = sky.meta["fam_size"]
     n_exp = sky.ex.n
@@ -172,15 +173,17 @@ def track_rms(ctx, sky, cand, device, chunk=65536):
     cover = ((true_xy[..., 0] >= -0.5) & (true_xy[..., 0] < W - 0.5) &
              (true_xy[..., 1] >= -0.5) & (true_xy[..., 1] < H - 0.5))
     cand = np.asarray(cand, np.int64)
-    out = np.empty(len(cand))
-    for s in range(0, len(cand), chunk):
-        c = cand[s:s + chunk]
+    out = np.full(len(cand), np.inf)                 # no injected asteroid: never a match
+    has = np.flatnonzero(cand // fam < len(sky.inj_states))
+    for s in range(0, len(has), chunk):
+        sel = has[s:s + chunk]
+        c = cand[sel]
         f = torch.as_tensor(c // fam, device=device)
         xy = _predict(ctx, sky.states[c], sky.t0, n_exp, device)
         d2 = ((xy - true_xy[f]) ** 2).sum(-1)
         cv = cover[f]
         rms = torch.sqrt(torch.where(cv, d2, torch.zeros_like(d2)).sum(1) / cv.sum(1).clamp(min=1))
-        out[s:s + chunk] = rms.cpu().numpy()
+        out[sel] = rms.cpu().numpy()
     return out
 
 
