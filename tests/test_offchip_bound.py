@@ -101,3 +101,78 @@ def test_gnomonic_stretch_within_45_degrees():
         worst = max(worst, stretch)
         assert stretch <= 1.0 / math.cos(math.radians(45.0)) ** 2 + 1e-6
     assert worst > 1.5                             # near 45 degrees the bound is nearly reached
+
+
+def _block_radius(r, v, tf, tm, h, obs_mid, d_obs, gm, inv_c):
+    """The persistent form's block cone (block_direction): predicted unit
+    direction at tm from the middle observer and its angular radius, in
+    FP32 where the kernel computes in FP32."""
+    f = np.float32
+    r32, v32 = r.astype(f), v.astype(f)
+    dt = f(tm - tf)
+    r2 = f(r32 @ r32)
+    ir = f(1.0) / np.sqrt(r2)
+    k = f(-gm) * ir * ir * ir
+    rho = (r32 + v32 * dt + f(0.5) * k * r32 * dt * dt - obs_mid.astype(f)).astype(f)
+    rr = f(np.sqrt(rho @ rho))
+    tau = (rr * f(1.01) + f(1e-3)) * f(inv_c)
+    hvec = np.cross(r, v)
+    p = hvec @ hvec / gm
+    alpha = 2 / np.linalg.norm(r) - v @ v / gm
+    e = math.sqrt(max(0.0, 1 - p * alpha))
+    q = p / (1 + e)
+    vq = math.sqrt(gm * (2 / q - alpha))
+    jerk6, half_acc = 4 * gm * vq / q ** 3 / 6, 0.5 * gm / q ** 2
+    adt = abs(float(dt)) + h
+    err = (jerk6 * adt ** 3 + half_acc * tau ** 2 + 1e-6 * (math.sqrt(r2) + rr) +
+           vq * (1e-6 * adt + 1e-4) + vq * (h + tau) + d_obs)
+    u = rho / rr
+    return u, (1.6 * err / (rr - err) if rr > 2 * err else math.inf)
+
+
+@pytest.mark.parametrize("kind", ["mba", "neo"])
+def test_block_cone_contains_every_sample_direction(kind):
+    """Every sample of a block (epochs within h of the middle one, observers
+    on the circular 1 AU orbit) lies inside the block cone: the angle between
+    the oracle's light-time corrected topocentric direction at t_j from o_j
+    and the predicted direction is at most the cone radius."""
+    rng = np.random.default_rng(21 if kind == "mba" else 22)
+    gm, c = O.gm_sun(), O.c_light()
+    worst = 0.0
+    for _ in range(120):
+        a = rng.uniform(2.1, 3.3) if kind == "mba" else rng.uniform(1.0, 2.0)
+        e = rng.uniform(0.0, 0.2) if kind == "mba" else rng.uniform(0.3, 0.6)
+        nu = rng.uniform(-math.pi, math.pi)
+        p = a * (1 - e * e)
+        rad = p / (1 + e * math.cos(nu))
+        hh = math.sqrt(gm * p)
+        pos = np.array([rad * math.cos(nu), rad * math.sin(nu), 0.0])
+        vel = np.array([-gm / hh * math.sin(nu), gm / hh * (e + math.cos(nu)), 0.0])
+        inc = math.radians(rng.uniform(0, 15))
+        R = np.array([[1, 0, 0], [0, math.cos(inc), -math.sin(inc)], [0, math.sin(inc), math.cos(inc)]])
+        r0, v0 = R @ pos, R @ vel
+        tf = 0.0
+        gap = rng.uniform(0.0, 12.0) * rng.choice([-1, 1])      # last FP64 state to block middle
+        h = rng.uniform(0.0, 1.0)
+        tm = tf + gap
+        ts = np.sort(np.concatenate([[tm - h, tm, tm + h], rng.uniform(tm - h, tm + h, 5)]))
+        th0 = rng.uniform(0, 2 * math.pi)
+        obs = np.stack([np.cos(th0 + 0.0172 * ts), np.sin(th0 + 0.0172 * ts), np.zeros_like(ts)], 1)
+        om = np.array([math.cos(th0 + 0.0172 * tm), math.sin(th0 + 0.0172 * tm), 0.0])
+        d_obs = float(np.max(np.linalg.norm(obs - om, axis=1))) * 1.0001 + 1e-7
+        u, radius = _block_radius(r0, v0, tf, tm, h, om, d_obs, gm, 1.0 / c)
+        if not math.isfinite(radius):
+            continue
+        for t, o in zip(ts, obs):
+            rho, _ = O.apparent(np.concatenate([r0, v0]), tf, t, o)
+            d = rho / np.linalg.norm(rho)
+            ang = 2 * math.asin(min(1.0, np.linalg.norm(d - u) / 2))
+            assert ang <= radius, (kind, gap, h, ang, radius)
+            worst = max(worst, ang / radius)
+    assert worst > 0.05                        # the radius is not vacuous
+
+
+def test_chord_angle_bound():
+    """2 asin(c / 2) <= 1.05 c for chords c <= 0.5 (the warp cone's radius)."""
+    c = np.linspace(1e-9, 0.5, 100001)
+    assert np.all(2 * np.arcsin(c / 2) <= 1.05 * c)
