@@ -75,7 +75,9 @@ def parse():
                    help="image side (default 4096 for mba, 2048 for batched)")
     p.add_argument("--n-exp", type=int, default=200)
     p.add_argument("--plane", default="bf16", choices=["f32", "bf16", "f16"])
-    p.add_argument("--forms", default="chosen,plain")
+    p.add_argument("--forms", default="chosen,plain,plain_fp64",
+                   help="chosen (BF16, persistent, graph, vetting), plain (FP32 planes, one thread "
+                        "per orbit), plain_fp64 (plain with FP64 light time and TAN projection)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -172,6 +174,8 @@ def make_workload(args, rank, device):
     if args.workload == "sparse":
         sky = synth.sparse_sky(seed=7 + rank)
         sky.fam_dev = None
+        # the orbits are seen around opposition, near t0: duplicates are judged there
+        sky.dedup_window = (sky.t0 - 20.0, sky.t0 + 20.0)
         imgs = synth.noise_images_torch(sky.ex, sky.seed, device)
         ctx = ndt.create(device.index, stream)
         try:
@@ -214,8 +218,9 @@ def make_workload(args, rank, device):
 
 
 class Form:
-    def __init__(self, name, plane, mode, graph, block=True):
+    def __init__(self, name, plane, mode, graph, block=True, geom64=False):
         self.name, self.plane, self.mode, self.graph, self.block = name, plane, mode, graph, block
+        self.geom64 = geom64
 
 
 NU_MIN = 5.0        # detection threshold of the candidate list (stacked SNR)
@@ -232,8 +237,9 @@ class Candidates:
     the list vetted by the CNN (ndt_vet) and by outlier trimming
     (ndt_trim_candidates)."""
 
-    def __init__(self, n, device, vet_params=None):
+    def __init__(self, n, device, vet_params=None, window=None):
         import torch
+        self.window = window
         self.idx = torch.empty(n, dtype=torch.int64, device=device)
         self.keep = torch.empty(n, dtype=torch.int64, device=device)
         self.vet_params = vet_params
@@ -247,7 +253,7 @@ class Candidates:
         self.m = ndt.count_candidates(ctx, NU_MIN)
         ndt.topk_candidates(ctx, self.m, self.idx)
         self.nk = ndt.dedup_candidates(ctx, states, t0, n, self.idx, self.m, self.keep,
-                                       radius_px=DEDUP_PX, n_ref=DEDUP_REFS)
+                                       radius_px=DEDUP_PX, n_ref=DEDUP_REFS, window=self.window)
         if self.vet_params is not None and self.nk > 0:
             lst = self.keep[:self.nk]
             ndt.vet(ctx, self.vet_params, states, t0, n, lst, self.scores[:self.nk])
@@ -386,7 +392,9 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
                          "sweep_ms": [round(float(t), 2) for t in times]}
             ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, ot, et, use_graph=form.graph)
         ndt.set_block_test(ctx, form.block)
-        cand = Candidates(n, device, vet_params if form.name == "chosen" else None)
+        ndt.set_fp64_geometry(ctx, form.geom64)
+        cand = Candidates(n, device, vet_params if form.name == "chosen" else None,
+                          getattr(sky, "dedup_window", None))
         run_steps(ctx, stream, sky, imgs, states, args.warmup, form.plane, cand)
         launches0 = ndt.get_stats(ctx)["kernel_launches"]
         barrier()
@@ -492,7 +500,7 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, cand_dev, form, barrier, dev
         for c in ctxs:
             if form.mode == "persistent":
                 ndt.set_launch(c, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"], use_graph=form.graph)
-        cands = [Candidates(n, device, vet_params) for _ in range(2)]
+        cands = [Candidates(n, device, vet_params, cand_dev.window) for _ in range(2)]
         st_dev = [torch.empty_like(states) for _ in range(2)]
         ref_list = cand_dev.keep[:cand_dev.nk].cpu().numpy()     # the device-input steps' list
         h_imgs = torch.empty(imgs.shape, dtype=imgs.dtype, pin_memory=True)
@@ -820,6 +828,7 @@ def main():
                                             survey_stamps=args.vet_survey_stamps)
     sky, stream, imgs, states = make_workload(args, rank, device)
     forms = {"plain": Form("plain", "f32", "plain", False),
+             "plain_fp64": Form("plain_fp64", "f32", "plain", False, geom64=True),
              "chosen": Form("chosen", args.plane, "persistent", True)}
     results, e2e = {}, None
     clocks = ClockSampler(local)

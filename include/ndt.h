@@ -249,6 +249,14 @@ ndt_status ndt_set_offchip_test(ndt_ctx *ctx, int32_t enabled);
    of the full computation.  enabled = 0 switches it off. */
 ndt_status ndt_set_block_test(ndt_ctx *ctx, int32_t enabled);
 
+/* All-FP64 geometry for the plain form (off by default): light time and the
+   TAN projection of stack_orbits in FP64 instead of double-float (FP32
+   pairs), with the nearest pixel from an FP64 floor; the propagated state is
+   FP64 in both.  The reference-precision variant the faster default is
+   measured against (positions agree to ~1e-7 px at 0.2 arcsec pixels).  The
+   persistent form always uses the double-float geometry. */
+ndt_status ndt_set_fp64_geometry(ndt_ctx *ctx, int32_t enabled);
+
 /*
  * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}
  * and exp_tile in {8, 16, 32} on the given workload (arguments as for
@@ -357,7 +365,10 @@ ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, in
  * cand_idx (n_cand indices into the orbit batch `states`, SoA 6 x n_orbits at
  * t0, host or device) is taken in rank order, best first, e.g. the output of
  * ndt_topk_candidates.  n_ref reference exposures are spread evenly over the
- * epoch-sorted exposures (first and last included); candidate i is a
+ * epoch-sorted exposures whose epochs lie in [t_lo, t_hi] (first and last
+ * of them included; every exposure when t_lo > t_hi or either is NaN, and
+ * NDT_EINVAL when the window holds none): a window around the epochs where
+ * the candidates are observed, in a survey far longer than that; candidate i is a
  * duplicate when some candidate ranked before it has predicted pixel
  * positions (same propagation, light time and TAN projection as the stack)
  * within radius_px of i's at every reference exposure, each in that
@@ -371,7 +382,7 @@ ndt_status ndt_trim_candidates(ndt_ctx *ctx, const double *states, double t0, in
  */
 ndt_status ndt_dedup_candidates(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
                                 const int64_t *cand_idx, int64_t n_cand, float radius_px, int32_t n_ref,
-                                int64_t *keep_idx, int64_t *n_keep);
+                                double t_lo, double t_hi, int64_t *keep_idx, int64_t *n_keep);
 
 /* vet: stamps of the candidates (as ndt_stamps) scored by the network:
    scores[i] = sigmoid(logit) in [0, 1]. */

@@ -86,6 +86,7 @@ struct ndt_ctx {
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
   int32_t offchip = 1;     // off-chip test of the persistent form
   int32_t block_test = 1;  // warp cone test per exposure block (persistent form)
+  int32_t geometry_fp64 = 0;  // plain form: FP64 light time and TAN projection
   float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
@@ -786,6 +787,7 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   a.t_ref = ctx->t_ref;
   a.offchip_test = persistent ? ctx->offchip : 0;
   a.block_test = persistent && ctx->offchip ? ctx->block_test : 0;
+  a.geometry_fp64 = persistent ? 0 : ctx->geometry_fp64;
   s = run_stack(ctx, a);
   if (s != NDT_OK) return s;
   ctx->last_n = n_orbits;
@@ -931,6 +933,12 @@ ndt_status ndt_set_offchip_test(ndt_ctx* ctx, int32_t enabled) {
   return NDT_OK;
 }
 
+ndt_status ndt_set_fp64_geometry(ndt_ctx* ctx, int32_t enabled) {
+  if (!ctx) return NDT_EINVAL;
+  ctx->geometry_fp64 = enabled ? 1 : 0;
+  return NDT_OK;
+}
+
 ndt_status ndt_set_block_test(ndt_ctx* ctx, int32_t enabled) {
   if (!ctx) return NDT_EINVAL;
   ctx->block_test = enabled ? 1 : 0;
@@ -1023,14 +1031,15 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
   const void* cd = nullptr;
   s = to_device(ctx, cand_idx, sizeof(int64_t) * n_cand, ctx->cand_stage, &cd);
   if (s != NDT_OK) return s;
-  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp), "stamp positions");
+  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp + sizeof(int) * n_cand), "stamp positions");
+  int* pos_cnt = reinterpret_cast<int*>(ctx->stamp_pos.as<int2>() + n_cand * ctx->n_exp);
   // reset the failure counter only: the valid-sample count of the last stack stays
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0,
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref,
                                 static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
-                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(),
+                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(), pos_cnt,
                                 ctx->counters.as<unsigned long long>(), ctx->stream), "stamp positions");
-  NDT_CK(launch_stamps(ctx->stamp_pos.as<int2>(), n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp,
+  NDT_CK(launch_stamps(ctx->stamp_pos.as<int2>(), pos_cnt, n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp,
                        ctx->planes.p, ctx->plane_type, f32_dev, bf16_dev, ctx->n_sms, ctx->stream),
          "stamp kernel");
   ctx->launches += 2;
@@ -1043,7 +1052,7 @@ extern "C" {
 
 ndt_status ndt_dedup_candidates(ndt_ctx* ctx, const double* states, double t0, int64_t n_orbits,
                                 const int64_t* cand_idx, int64_t n_cand, float radius_px, int32_t n_ref,
-                                int64_t* keep_idx, int64_t* n_keep) {
+                                double t_lo, double t_hi, int64_t* keep_idx, int64_t* n_keep) {
   if (!ctx) return NDT_EINVAL;
   NDT_CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   if (ctx->n_exp < 1) return fail(ctx, NDT_ESTATE, "dedup before load_exposures");
@@ -1055,11 +1064,18 @@ ndt_status ndt_dedup_candidates(ndt_ctx* ctx, const double* states, double t0, i
     return fail(ctx, NDT_EINVAL, "radius %g or n_ref %d out of range", radius_px, n_ref);
   *n_keep = 0;
   if (n_cand == 0) return NDT_OK;
-  // reference exposures: evenly spread over the epoch-sorted exposures
+  // reference exposures: evenly spread over the epoch-sorted exposures with
+  // epochs in [t_lo, t_hi] (every exposure when the window is empty or NaN)
+  int32_t lo = 0, hi = ctx->n_exp - 1;
+  if (t_lo <= t_hi) {
+    while (lo < ctx->n_exp && ctx->ex_host[lo].t < t_lo) ++lo;
+    while (hi >= 0 && ctx->ex_host[hi].t > t_hi) --hi;
+    if (lo > hi) return fail(ctx, NDT_EINVAL, "no exposure with an epoch in [%g, %g]", t_lo, t_hi);
+  }
+  const int32_t m = hi - lo + 1;
   std::vector<int32_t> ref;
   for (int k = 0; k < n_ref; ++k) {
-    const int32_t pos = n_ref == 1 ? (ctx->n_exp - 1) / 2
-                                   : (int32_t)std::lround((double)k * (ctx->n_exp - 1) / (n_ref - 1));
+    const int32_t pos = lo + (n_ref == 1 ? (m - 1) / 2 : (int32_t)std::lround((double)k * (m - 1) / (n_ref - 1)));
     if (ref.empty() || pos > ref.back()) ref.push_back(pos);
   }
   const int nr = (int)ref.size();
@@ -1187,14 +1203,15 @@ ndt_status ndt_trim_candidates(ndt_ctx* ctx, const double* states, double t0, in
   int32_t* nk = nullptr;
   if ((s = out_buffer(ctx, nu_out, (size_t)n_cand, ctx->trim_nu, &nu)) != NDT_OK) return s;
   if ((s = out_buffer(ctx, nkept_out, (size_t)n_cand, ctx->trim_n, &nk)) != NDT_OK) return s;
-  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp), "trim positions");
+  NDT_CK(ctx->stamp_pos.ensure(sizeof(int2) * n_cand * ctx->n_exp + sizeof(int) * n_cand), "trim positions");
+  int* pos_cnt = reinterpret_cast<int*>(ctx->stamp_pos.as<int2>() + n_cand * ctx->n_exp);
   NDT_CK(ctx->trim_bits.ensure(4 * trim_scratch_words(n_cand, ctx->n_exp)), "trim scratch");
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0,
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref,
                                 static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
-                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(),
+                                ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(), pos_cnt,
                                 ctx->counters.as<unsigned long long>(), ctx->stream), "trim positions");
-  NDT_CK(launch_trim(ctx->stamp_pos.as<int2>(), n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp, ctx->planes.p,
+  NDT_CK(launch_trim(ctx->stamp_pos.as<int2>(), pos_cnt, n_cand, ctx->ex_dev.as<ExpDev>(), ctx->n_exp, ctx->planes.p,
                      ctx->plane_type, kappa, max_iter, min_obs, ctx->trim_bits.as<uint32_t>(), nu, nk, nullptr,
                      nullptr, ctx->n_sms, ctx->stream),
          "trim kernel");

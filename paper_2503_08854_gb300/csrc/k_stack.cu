@@ -135,18 +135,20 @@ __device__ __forceinline__ unsigned warp_block_mask(const Walk& w, const Phys& p
   for (int o = 16; o > 0; o >>= 1) th = fmaxf(th, __shfl_xor_sync(full, th, o));
   if (!(th < 1.0f)) return 0u;
   float sr, cr;
-  sincosf(th, &sr, &cr);
+  __sincosf(th, &sr, &cr);                     // abs. error ~1e-6 for |th| < 1, inside the slack below
   bool miss = false;
   if (lane < cnt) {
     const ExpDev& e = blk[lane];
     const float cd = c[0] * e.p0_f[0] + c[1] * e.p0_f[1] + c[2] * e.p0_f[2];
     // cos(th + R) = cos th cos R - sin th sin R, with th + R < 2.5 < pi
-    miss = e.chip_cos > 0.0707f && cd < fmaf(cr, e.chip_cos, -sr * e.chip_sin) - 1e-6f;
+    miss = e.chip_cos > 0.0707f && cd < fmaf(cr, e.chip_cos, -sr * e.chip_sin) - 1e-5f;
   }
   return __ballot_sync(full, miss) & all;
 }
 
-template <int PT, bool FP32_COPY = false>
+// GEOM64: light time and TAN projection in FP64 (apparent_rho_d, project_h
+// and an FP64 floor) instead of double-float.
+template <int PT, bool FP32_COPY = false, bool GEOM64 = false>
 __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDev& e,
                                             const void* __restrict__ planes) {
   if (w.failed) return;
@@ -157,10 +159,24 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
   }
   w.t_prev = e.t;
   if (FP32_COPY) walk_fp32_copy(w, e.tf);
-  dfloat rho[3];
-  apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rho);
   int ix, iy;
-  if (pixel_of(e, rho, ix, iy)) {
+  bool in;
+  if constexpr (GEOM64) {
+    double rho[3], xh, yh;
+    apparent_rho_d(ph, w.r, w.v, w.inv_r, e, rho);
+    in = project_h(e, rho, xh, yh);
+    if (in) {
+      const double fx = floor(xh), fy = floor(yh);
+      in = fx >= 0.0 && fx < (double)e.W && fy >= 0.0 && fy < (double)e.H;
+      ix = (int)fx;
+      iy = (int)fy;
+    }
+  } else {
+    dfloat rho[3];
+    apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rho);
+    in = pixel_of(e, rho, ix, iy);
+  }
+  if (in) {
     const float2 pv = gather_plane<PT>(planes, e, ix, iy);
     w.sp.add(pv.x);
     w.sf.add(pv.y);
@@ -200,7 +216,7 @@ __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, i
 }
 
 // Plain form: one thread per orbit, grid covers all orbits.
-template <int PT>
+template <int PT, bool GEOM64>
 __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const StackArgs a) {
   const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const bool active = o < a.n;
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const St
     }
     for (int64_t k = e_begin; k < e_end; ++k) {
       const int j = a.n_fam > 0 ? __ldg(a.fam_exp_pos + k) : (int)k;
-      walk_sample<PT>(w, a.ph, a.ex[j], a.planes);
+      walk_sample<PT, false, GEOM64>(w, a.ph, a.ex[j], a.planes);
     }
   }
   walk_finish(w, a, o, active);
@@ -270,6 +286,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
       w.failed = true;   // no orbit: votes "off-chip" and does no work
     }
     constexpr int kWords = (int)(sizeof(ExpDev) / 8);
+    int backoff = 0, backoff_left = 0;         // warp-uniform
     for (int64_t eb = e_begin; eb < e_end; eb += ET) {
       const int cnt = (int)min((int64_t)ET, e_end - eb);
       // stage cnt exposure records (kWords 8-byte words each) into shared memory
@@ -280,8 +297,19 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
         dst[i] = __ldg(reinterpret_cast<const double*>(a.ex + j) + wd);
       }
       team_sync<TEAM>(team);
-      // exposures of the block that no orbit of this warp can reach
-      const unsigned miss = a.block_test ? warp_block_mask(w, a.ph, stage[team], cnt, active) : 0u;
+      // exposures of the block that no orbit of this warp can reach; after a
+      // block where the test removed nothing, the warp skips the test for 1,
+      // 2, 4, ... up to 8 blocks (dense fields, where every chip is in reach)
+      unsigned miss = 0u;
+      if (a.block_test) {
+        if (backoff_left > 0) {
+          --backoff_left;
+        } else {
+          miss = warp_block_mask(w, a.ph, stage[team], cnt, active);
+          backoff = miss ? 0 : min(2 * backoff + 1, 8);
+          backoff_left = backoff;
+        }
+      }
       // every lane runs the loop: the off-chip vote is warp-wide
       for (int jj = 0; jj < cnt; ++jj) {
         const ExpDev& e = stage[team][jj];
@@ -359,9 +387,15 @@ cudaError_t launch_persistent_pt(const StackArgs& a, int n_sms, cudaStream_t st)
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st) {
   const int64_t blocks = (a.n + kBlock - 1) / kBlock;
   if (blocks == 0) return cudaSuccess;
-  if (a.plane_type == kF32) k_stack_plain<kF32><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-  else if (a.plane_type == kBF16) k_stack_plain<kBF16><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-  else k_stack_plain<kF16><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  if (a.geometry_fp64) {
+    if (a.plane_type == kF32) k_stack_plain<kF32, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else if (a.plane_type == kBF16) k_stack_plain<kBF16, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else k_stack_plain<kF16, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  } else {
+    if (a.plane_type == kF32) k_stack_plain<kF32, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else if (a.plane_type == kBF16) k_stack_plain<kBF16, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+    else k_stack_plain<kF16, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

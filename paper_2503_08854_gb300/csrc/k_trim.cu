@@ -36,32 +36,34 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Entry k of a candidate's compacted positions: (ix << 16 | exposure, iy).
 template <int PT>
 __device__ __forceinline__ bool intersection(const int2* __restrict__ cpos, const ExpDev* __restrict__ ex,
-                                             const void* __restrict__ planes, int j, float2& v) {
-  const int2 p = cpos[j];
-  if (p.x == INT_MIN) return false;
-  v = gather_plane<PT>(planes, ex[j], p.x, p.y);
+                                             const void* __restrict__ planes, int k, float2& v) {
+  const int2 p = cpos[k];
+  v = gather_plane<PT>(planes, ex[p.x & 0xffff], p.x >> 16, p.y);
   return v.y > 0.0f;
 }
 
 template <int PT>
 __global__ void __launch_bounds__(kTrimWarps * 32)
-    k_trim(const int2* __restrict__ pos, int64_t n_cand, const ExpDev* __restrict__ ex, int32_t n_exp,
+    k_trim(const int2* __restrict__ pos, const int* __restrict__ pos_cnt, int64_t n_cand,
+           const ExpDev* __restrict__ ex, int32_t n_exp,
            const void* __restrict__ planes, float kappa, int32_t max_iter, int32_t min_obs,
            uint32_t* __restrict__ keep_bits, float* __restrict__ nu_out, int32_t* __restrict__ n_out,
            float* __restrict__ psi_out, float* __restrict__ phi_out) {
   const int lane = threadIdx.x & 31;
-  const int64_t n_words = (n_exp + 31) / 32;
   for (int64_t c = (int64_t)blockIdx.x * kTrimWarps + (threadIdx.x >> 5); c < n_cand;
        c += (int64_t)gridDim.x * kTrimWarps) {
     const int2* cpos = pos + c * n_exp;
-    uint32_t* bits = keep_bits + c * n_words;
+    const int m = pos_cnt[c];                     // the candidate's in-image intersections
+    const int64_t n_words = (m + 31) / 32;
+    uint32_t* bits = keep_bits + c * ((n_exp + 31) / 32);
     // round 0 keeps every valid intersection
     for (int64_t w = 0; w < n_words; ++w) {
       const int j = (int)(w * 32) + lane;
       float2 v;
-      const bool ok = j < n_exp && intersection<PT>(cpos, ex, planes, j, v);
+      const bool ok = j < m && intersection<PT>(cpos, ex, planes, j, v);
       const uint32_t word = __ballot_sync(0xffffffffu, ok);
       if (lane == 0) bits[w] = word;
     }
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(kTrimWarps * 32)
         const int j = (int)(w * 32) + lane;
         float2 v;
         bool keep = false;
-        if (j < n_exp && intersection<PT>(cpos, ex, planes, j, v)) {
+        if (j < m && intersection<PT>(cpos, ex, planes, j, v)) {
           const float rs = __fsqrt_rn(v.y);
           keep = __fdiv_rn(v.x, rs) - a_hat * rs <= kappa;
         }
@@ -130,7 +132,8 @@ __global__ void __launch_bounds__(kTrimWarps * 32)
 
 size_t trim_scratch_words(int64_t n_cand, int32_t n_exp) { return (size_t)n_cand * ((n_exp + 31) / 32); }
 
-cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp, const void* planes,
+cudaError_t launch_trim(const int2* pos, const int* pos_cnt, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+                        const void* planes,
                         int plane_type, float kappa, int32_t max_iter, int32_t min_obs, uint32_t* keep_bits,
                         float* nu_out, int32_t* n_out, float* psi_out, float* phi_out, int n_sms,
                         cudaStream_t st) {
@@ -139,13 +142,13 @@ cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32
   const unsigned blocks = (unsigned)std::min<int64_t>(want, (int64_t)n_sms * 16);
   const unsigned threads = kTrimWarps * 32;
   if (plane_type == kF32)
-    k_trim<kF32><<<blocks, threads, 0, st>>>(pos, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
+    k_trim<kF32><<<blocks, threads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
                                               keep_bits, nu_out, n_out, psi_out, phi_out);
   else if (plane_type == kBF16)
-    k_trim<kBF16><<<blocks, threads, 0, st>>>(pos, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
+    k_trim<kBF16><<<blocks, threads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
                                                keep_bits, nu_out, n_out, psi_out, phi_out);
   else
-    k_trim<kF16><<<blocks, threads, 0, st>>>(pos, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
+    k_trim<kF16><<<blocks, threads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, kappa, max_iter, min_obs,
                                               keep_bits, nu_out, n_out, psi_out, phi_out);
   return cudaGetLastError();
 }

@@ -41,17 +41,25 @@ static_assert(NPARAM == 52929, "parameter layout");
 
 // ------------------------------------------------------------------ stamps --
 
+// Positions along each candidate's track, compacted: entry k < cnt[i] of
+// candidate i is (ix << 16 | j, iy) for its k-th exposure j
+// (in epoch order) whose nearest pixel lies inside the image.  Before each
+// FP64 step, the FP32 off-chip test of the persistent stack
+// (certainly_off_chip, from the last computed state) removes the exposures
+// the track certainly misses: the state stays at its last epoch, and the
+// next computed step is longer (still exact).  In a sparse survey this
+// removes almost every step.
 __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ states, int64_t n,
-                                                   double t0, const int64_t* __restrict__ cand,
+                                                   double t0, double t_ref, const int64_t* __restrict__ cand,
                                                    int64_t n_cand, const ExpDev* __restrict__ ex,
                                                    int32_t n_exp, Phys ph, int2* __restrict__ pos,
-                                                   unsigned long long* counters) {
+                                                   int* __restrict__ cnt, unsigned long long* counters) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cand) return;
   const int64_t o = cand[i];
   int2* out = pos + i * n_exp;
   if (o < 0 || o >= n) {
-    for (int j = 0; j < n_exp; ++j) out[j] = make_int2(INT_MIN, INT_MIN);
+    cnt[i] = 0;
     return;
   }
   double r[3], v[3];
@@ -63,24 +71,31 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
   double inv_r = 1.0 / rn;
   const OrbitConst oc = orbit_const(ph, r, v, inv_r);
   double t_prev = t0;
-  bool failed = false;
+  float rf[3], vf[3], tf = (float)(t0 - t_ref);
+  for (int c = 0; c < 3; ++c) {
+    rf[c] = d2f_trunc(r[c]);
+    vf[c] = d2f_trunc(v[c]);
+  }
+  int k = 0;
   for (int j = 0; j < n_exp; ++j) {
     const ExpDev& e = ex[j];
-    int2 p = make_int2(INT_MIN, INT_MIN);
-    if (!failed) {
-      if (kepler_step(ph, oc, e.t - t_prev, r, v, rn, inv_r) < 0) {
-        failed = true;
-        atomicAdd(counters + 1, 1ull);
-      } else {
-        t_prev = e.t;
-        dfloat rho[3];
-        int ix, iy;
-        apparent_rho_df(ph, r, v, inv_r, e, rho);
-        if (pixel_of(e, rho, ix, iy)) p = make_int2(ix, iy);
-      }
+    if (certainly_off_chip(ph, oc, rf, vf, tf, e)) continue;
+    if (kepler_step(ph, oc, e.t - t_prev, r, v, rn, inv_r) < 0) {
+      atomicAdd(counters + 1, 1ull);
+      break;
     }
-    out[j] = p;
+    t_prev = e.t;
+    tf = e.tf;
+    for (int c = 0; c < 3; ++c) {
+      rf[c] = d2f_trunc(r[c]);
+      vf[c] = d2f_trunc(v[c]);
+    }
+    dfloat rho[3];
+    int ix, iy;
+    apparent_rho_df(ph, r, v, inv_r, e, rho);
+    if (pixel_of(e, rho, ix, iy)) out[k++] = make_int2((ix << 16) | j, iy);   // j < 2^16, ix < 2^15
   }
+  cnt[i] = k;
 }
 
 // One thread per stamp pixel (448 threads, 441 active); exposures are taken
@@ -95,7 +110,8 @@ constexpr int kStampUnroll = 4;
 constexpr int kStampThreads = 448;
 
 template <int PT>
-__global__ void __launch_bounds__(kStampThreads) k_stamps(const int2* __restrict__ pos, int64_t n_cand,
+__global__ void __launch_bounds__(kStampThreads) k_stamps(const int2* __restrict__ pos,
+                                                          const int* __restrict__ pos_cnt, int64_t n_cand,
                                                           const ExpDev* __restrict__ ex, int32_t n_exp,
                                                           const void* __restrict__ planes,
                                                           float* __restrict__ out_f32,
@@ -106,19 +122,19 @@ __global__ void __launch_bounds__(kStampThreads) k_stamps(const int2* __restrict
     float sp = 0.0f, sf = 0.0f, sq = 0.0f;
     int cnt = 0;
     const int2* cpos = pos + c * n_exp;
-    for (int j0 = 0; j0 < n_exp; j0 += kStampUnroll) {
+    const int m = pos_cnt[c];
+    for (int k0 = 0; k0 < m; k0 += kStampUnroll) {
       float2 v[kStampUnroll];
       bool ok[kStampUnroll];
 #pragma unroll
       for (int u = 0; u < kStampUnroll; ++u) {
-        const int j = j0 + u;
+        const int k = k0 + u;
         ok[u] = false;
         v[u] = make_float2(0.0f, 0.0f);
-        if (j >= n_exp || p >= NPIX) continue;
-        const int2 ctr = cpos[j];
-        if (ctr.x == INT_MIN) continue;
-        const ExpDev& e = ex[j];
-        const int px = ctr.x + dx, py = ctr.y + dy;
+        if (k >= m || p >= NPIX) continue;
+        const int2 ctr = cpos[k];
+        const ExpDev& e = ex[ctr.x & 0xffff];
+        const int px = (ctr.x >> 16) + dx, py = ctr.y + dy;
         if ((unsigned)px >= (unsigned)e.W || (unsigned)py >= (unsigned)e.H) continue;
         v[u] = gather_plane<PT>(planes, e, px, py);
         ok[u] = true;
@@ -440,30 +456,31 @@ cudaError_t launch_sigmoid(float* z, int64_t n, cudaStream_t st) {
 int cnn_param_count() { return NPARAM; }
 size_t cnn_smem_bytes() { return kCnnSmem; }
 
-cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, const int64_t* cand,
-                                   int64_t n_cand, const ExpDev* ex, int32_t n_exp, Phys ph,
-                                   int2* pos, unsigned long long* counters, cudaStream_t st) {
+cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref,
+                                   const int64_t* cand, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+                                   Phys ph, int2* pos, int* cnt, unsigned long long* counters,
+                                   cudaStream_t st) {
   // one warp per block while the candidates do not fill every SM with four
   // 128-thread blocks, so that they spread over all SMs (FP64-bound threads)
   const int threads = n_cand < 128 * 4 * 152 ? 32 : 128;
   const int64_t blocks = (n_cand + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
-  k_stamp_pos<<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, cand, n_cand, ex, n_exp, ph, pos,
-                                                    counters);
+  k_stamp_pos<<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, n_exp, ph, pos,
+                                                    cnt, counters);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+cudaError_t launch_stamps(const int2* pos, const int* pos_cnt, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                           const void* planes, int plane_type, float* out_f32,
                           __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st) {
   if (n_cand == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>(n_cand, (int64_t)n_sms * 16);
   if (plane_type == kF32)
-    k_stamps<kF32><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kF32><<<blocks, kStampThreads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   else if (plane_type == kBF16)
-    k_stamps<kBF16><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kBF16><<<blocks, kStampThreads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   else
-    k_stamps<kF16><<<blocks, kStampThreads, 0, st>>>(pos, n_cand, ex, n_exp, planes, out_f32, out_bf16);
+    k_stamps<kF16><<<blocks, kStampThreads, 0, st>>>(pos, pos_cnt, n_cand, ex, n_exp, planes, out_f32, out_bf16);
   return cudaGetLastError();
 }
 

@@ -494,6 +494,28 @@ __device__ __forceinline__ void apparent_rho_df(const Phys& ph, const double r[3
   }
 }
 
+// The same light-time model in FP64 throughout (the all-FP64 geometry of
+// the plain form's reference variant): rho = d - tau v - (tau^2/2) u r +
+// (tau^3/6) u (v - 3 p r), tau = |d|/c - (d.v)/c^2 + (|d| v^2 + (d.v)^2/|d|
+// - u |d| (d.r)) / (2 c^3).
+__device__ __forceinline__ void apparent_rho_d(const Phys& ph, const double r[3], const double v[3],
+                                               double inv_r, const ExpDev& e, double rho[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rho[i] = r[i] - e.obs[i];
+  if (ph.inv_c == 0.0f) return;
+  const double ic = (double)ph.inv_c + (double)ph.inv_c_l;
+  const double dist = sqrt(rho[0] * rho[0] + rho[1] * rho[1] + rho[2] * rho[2]);
+  const double dv = rho[0] * v[0] + rho[1] * v[1] + rho[2] * v[2];
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double u = ph.force_free ? 0.0 : ph.gm * inv_r * inv_r * inv_r;
+  const double dr = rho[0] * r[0] + rho[1] * r[1] + rho[2] * r[2];
+  const double p = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * inv_r * inv_r;
+  const double tau = dist * ic - dv * ic * ic + 0.5 * ic * ic * ic * (dist * (v2 - u * dr) + dv * dv / dist);
+  const double h = -0.5 * u * tau * tau, k = u * tau * tau * tau * kInv6;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rho[i] += -tau * v[i] + h * r[i] + k * (v[i] - 3.0 * p * r[i]);
+}
+
 // TAN projection through the precomputed per-exposure rows (Calabretta &
 // Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
 // Gives the pixel coordinates shifted by one half, (x + 1/2, y + 1/2), so
@@ -706,6 +728,7 @@ struct StackArgs {
   double t_ref;                // epoch origin of ExpDev::tf
   int32_t offchip_test;        // persistent form: skip FP64 work of certainly off-chip samples
   int32_t block_test;          // persistent form: warp cone test per staged exposure block
+  int32_t geometry_fp64;       // plain form: FP64 light time and TAN projection
 };
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);
@@ -736,11 +759,15 @@ cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64
 int cnn_param_count();
 size_t cnn_smem_bytes();
 int cnn_backward_blocks(int64_t n, int n_sms);
-cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, const int64_t* cand,
-                                   int64_t n_cand, const ExpDev* ex, int32_t n_exp, Phys ph,
-                                   int2* pos, unsigned long long* counters, cudaStream_t st);
-cudaError_t launch_stamps(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
-                          const void* planes, int plane_type, float* out_f32,
+// Compacted track positions of candidates: pos[i * n_exp + k], k < cnt[i],
+// = (ix << 16 | exposure, iy) of the k-th exposure (epoch order) whose
+// nearest pixel is inside the image (exposures < 2^16, widths <= 2^15).
+cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref,
+                                   const int64_t* cand, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+                                   Phys ph, int2* pos, int* cnt, unsigned long long* counters,
+                                   cudaStream_t st);
+cudaError_t launch_stamps(const int2* pos, const int* pos_cnt, int64_t n_cand, const ExpDev* ex,
+                          int32_t n_exp, const void* planes, int plane_type, float* out_f32,
                           __nv_bfloat16* out_bf16, int n_sms, cudaStream_t st);
 // Iterative-MAD noise estimate (k_mad.cu): one image and its round state.
 struct MadImage {
@@ -762,7 +789,8 @@ cudaError_t launch_mad_round(const MadImage* imgs, MadState* st, uint32_t* hist,
 size_t mad_hist_words(int n_images);
 
 size_t trim_scratch_words(int64_t n_cand, int32_t n_exp);
-cudaError_t launch_trim(const int2* pos, int64_t n_cand, const ExpDev* ex, int32_t n_exp, const void* planes,
+cudaError_t launch_trim(const int2* pos, const int* pos_cnt, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
+                        const void* planes,
                         int plane_type, float kappa, int32_t max_iter, int32_t min_obs, uint32_t* keep_bits,
                         float* nu_out, int32_t* n_out, float* psi_out, float* phi_out, int n_sms,
                         cudaStream_t st);

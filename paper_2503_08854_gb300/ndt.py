@@ -78,8 +78,10 @@ _lib.ndt_cnn_adam_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i64, _i32, C.c_floa
 _lib.ndt_vet.argtypes = [_vp, _vp, _vp, _f64, _i64, _vp, _i64, _vp]
 _lib.ndt_synchronize.argtypes = [_vp]
 _lib.ndt_topk_noalloc.argtypes = [_vp, _i64, _i64, _vp, _vp, _vp]
-_lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _vp, C.POINTER(_i64)]
+_lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float, _i32, _f64, _f64, _vp,
+                                      C.POINTER(_i64)]
 _lib.ndt_set_block_test.argtypes = [_vp, _i32]
+_lib.ndt_set_fp64_geometry.argtypes = [_vp, _i32]
 _lib.ndt_count_candidates.argtypes = [_vp, C.c_float, C.POINTER(_i64)]
 _lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
@@ -304,6 +306,11 @@ def topk_noalloc(snr, n, k, idx_out=None, snr_out=None, stream=None):
         raise NdtError(st, "ndt_topk_noalloc rejected the call (sizes, or non-device pointers)")
 
 
+def set_fp64_geometry(ctx, enabled=True):
+    """ndt_set_fp64_geometry: FP64 light time and TAN projection in the plain form."""
+    _check(ctx, _lib.ndt_set_fp64_geometry(ctx, 1 if enabled else 0))
+
+
 def set_block_test(ctx, enabled=True):
     """ndt_set_block_test: the persistent form's per-warp cone test of each
     staged exposure block."""
@@ -317,14 +324,17 @@ def count_candidates(ctx, min_snr):
     return c.value
 
 
-def dedup_candidates(ctx, states_soa, t0, n_orbits, cand_idx, n_cand, keep_idx, radius_px=4.0, n_ref=3):
+def dedup_candidates(ctx, states_soa, t0, n_orbits, cand_idx, n_cand, keep_idx, radius_px=4.0, n_ref=3,
+                     window=None):
     """ndt_dedup_candidates: keep_idx[:returned] = the candidates of cand_idx
     (rank order) with no better-ranked candidate within radius_px at every
-    reference exposure; returns that number."""
+    reference exposure (spread over the exposures with epochs in ``window``
+    = (t_lo, t_hi), or over all of them); returns that number."""
+    t_lo, t_hi = (1.0, 0.0) if window is None else (float(window[0]), float(window[1]))
     nk = C.c_int64()
     _check(ctx, _lib.ndt_dedup_candidates(ctx, _ptr(states_soa), float(t0), int(n_orbits), _ptr(cand_idx),
-                                          int(n_cand), float(radius_px), int(n_ref), _ptr(keep_idx),
-                                          C.byref(nk)))
+                                          int(n_cand), float(radius_px), int(n_ref), t_lo, t_hi,
+                                          _ptr(keep_idx), C.byref(nk)))
     return nk.value
 
 
@@ -350,4 +360,4 @@ def exported_symbols():
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
             "ndt_measure_fp64_rate", "ndt_dedup_candidates", "ndt_count_candidates",
-            "ndt_set_block_test"]
+            "ndt_set_block_test", "ndt_set_fp64_geometry"]

@@ -32,18 +32,21 @@ def _clusters(seed, n_centres=12, per=120, pos_sig=4e-6, vel_sig=2e-7):
     return sky, states, rank
 
 
-@pytest.mark.parametrize("n_ref,radius", [(3, 4.0), (1, 2.5), (5, 8.0)])
-def test_dedup_matches_oracle(gpu, n_ref, radius):
+@pytest.mark.parametrize("n_ref,radius,windowed", [(3, 4.0, False), (1, 2.5, False), (5, 8.0, False),
+                                                   (3, 4.0, True)])
+def test_dedup_matches_oracle(gpu, n_ref, radius, windowed):
     sky, states, rank = _clusters(5)
     gpu.load(sky.ex, np.zeros((sky.ex.n, 512, 512), np.float32))
     n = len(rank)
+    t = np.sort(sky.ex.mjd)
+    window = (0.5 * (t[1] + t[2]), 0.5 * (t[6] + t[7])) if windowed else None
     cand = torch.as_tensor(rank, dtype=torch.int64, device=gpu.dev)
     out = torch.full((n,), -1, dtype=torch.int64, device=gpu.dev)
     nk = ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), cand, n, out,
-                              radius_px=radius, n_ref=n_ref)
+                              radius_px=radius, n_ref=n_ref, window=window)
     got = out[:nk].cpu().numpy()
     assert bool((out[nk:] == -1).all())
-    ref, dist = OD.dedup(states, sky.t0, sky.ex, rank, radius, n_ref)
+    ref, dist = OD.dedup(states, sky.t0, sky.ex, rank, radius, n_ref, window)
     # each candidate's fate depends only on the distances to those ranked
     # before it: compare every candidate whose decision does not hinge on a
     # distance within 2e-4 px of the radius (FP32 coordinates on the GPU,
@@ -75,6 +78,8 @@ def test_dedup_host_pointers_and_edges(gpu):
         ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), one, 2, o2, radius_px=0.0)
     with pytest.raises(ndt.NdtError):
         ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), one, 2, o2, n_ref=9)
+    with pytest.raises(ndt.NdtError):           # a window without exposures
+        ndt.dedup_candidates(gpu.ctx, gpu.soa(states), sky.t0, len(states), one, 2, o2, window=(0.0, 1.0))
 
 
 def test_count_candidates_matches_oracle_nu(gpu):

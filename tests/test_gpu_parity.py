@@ -260,6 +260,24 @@ def test_plain_workload_stack_and_top100(gpu):
         check_topk(idx3, val3, nu, ref["n_amb"] > 0, k)
 
 
+def test_fp64_geometry_form_matches_oracle(gpu):
+    """The plain form with FP64 light time and TAN projection (the reference-
+    precision variant) on the tiny workload: element-wise parity with the
+    oracle, and the same in-bounds samples as the double-float default."""
+    sky = synth.grid_sky()
+    imgs = _images(sky)
+    gpu.load(sky.ex, imgs)
+    pl = [O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j]) for j in range(sky.ex.n)]
+    ref = O.stack(sky.states, sky.t0, sky.ex, planes=([p[0] for p in pl], [p[1] for p in pl]))
+    ndt.set_fp64_geometry(gpu.ctx, True)
+    out64 = gpu.stack(sky.states, sky.t0)
+    check_stack(out64, ref)
+    ndt.set_fp64_geometry(gpu.ctx, False)
+    out = gpu.stack(sky.states, sky.t0)
+    clean = ref["n_amb"] == 0
+    assert np.array_equal(out64["nobs"][clean], out["nobs"][clean])
+
+
 def _families(rng, n_orb, n_exp, n_fam):
     cuts = np.sort(rng.choice(np.arange(1, n_orb), n_fam - 1, replace=False))
     fo = np.concatenate([[0], cuts, [n_orb]]).astype(np.int64)

@@ -21,6 +21,16 @@ def test_reference_positions_hand_worked():
     assert list(D.reference_positions(ex.subset([3, 1]), 3)) == [1, 0]
 
 
+def test_reference_positions_in_a_window():
+    ex = synth.grid_sky(n_exp=10, size=64, n_r=1, n_v=2, seed=1).ex
+    order = np.argsort(ex.mjd, kind="stable")
+    t = ex.mjd[order]
+    # a window holding sorted positions 3..7 (m = 5): 3, 3 + round(2) = 5, 7
+    w = (0.5 * (t[2] + t[3]), 0.5 * (t[7] + t[8]))
+    assert list(D.reference_positions(ex, 3, w)) == list(order[[3, 5, 7]])
+    assert list(D.reference_positions(ex, 1, w)) == [order[5]]
+
+
 def test_reference_positions_follow_epoch_order():
     ex = synth.grid_sky(n_exp=5, size=64, n_r=1, n_v=2, seed=1).ex
     perm = np.array([3, 0, 4, 1, 2])
