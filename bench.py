@@ -42,21 +42,42 @@ UNIT = "samples/s"
 # is the FP64-pipe time the launch needs (instructions per computed sample x
 # computed samples / that rate) over its measured time.
 FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
-# FP64 flops executed per computed (orbit, exposure) sample by the stack
-# kernel, from ncu instruction counters (DFMA x 2 + DADD + DMUL) over the
-# samples whose FP64 work ran in the captured launch (samples minus those the
-# off-chip test removed), and the FP64-pipe thread instructions per computed
-# sample (conversions and compares included).  MBA: workload at 512 orbits per
-# family and 1024 x 1024 images; batched: 128 families and 512 x 512 images.
-# MBA: 8.637e7 computed samples, 24.21 DFMA + 12.86 DMUL + 1.99 DADD each;
-# batched: 2.037e8 computed samples, 32.06 DFMA + 18.23 DMUL + 2.04 DADD.
-FP64_PER_SAMPLE = {"mba": (63.3, 39.6), "batched": (84.4, 53.3)}
-# The same counts split by instruction (DFMA, DMUL, DADD per computed sample).
-FP64_MIX = {"mba": (24.21, 12.86, 1.99), "batched": (32.06, 18.23, 2.04)}
-# DRAM bytes (read + write) of one full-size persistent stack launch (BF16
-# planes, off-chip test on), ncu dram__bytes_read.sum + dram__bytes_write.sum
-# in a one-pass capture: MBA 1.857 GB + 71.1 MB, batched 3.528 GB + 273.0 MB.
-TRAFFIC_BYTES_PER_LAUNCH = {"mba": 1.9279e9, "batched": 3.8012e9}
+# FP64 work per computed (orbit, exposure) sample of each stack kernel form,
+# from ncu thread-instruction counters (smsp__sass_thread_inst_executed_op_
+# {dfma,dmul,dadd}_pred_on.sum) over the samples whose FP64 work ran in the
+# captured launch (samples minus those the off-chip and block tests removed):
+# (DFMA, DMUL, DADD) per computed sample; flops = 2 DFMA + DMUL + DADD.
+# MBA: the workload at 512 orbits per family and 1024 x 1024 images (1.024e8
+# samples; chosen 8.637e7 computed); batched: 128 families and 512 x 512
+# images (chosen 2.022e8 computed samples; its FP64-state figure, 2.037e8,
+# predates the block test).
+FP64_MIX = {("mba", "chosen"): (0.760, 0.324, 0.041),
+            ("batched", "chosen"): (6.589, 3.657, 0.760),
+            ("mba", "chosen_fp64_state"): (24.21, 13.56, 1.99),
+            ("mba", "plain"): (23.27, 12.05, 1.99),
+            ("mba", "plain_fp64"): (68.27, 43.06, 8.00),
+            ("batched", "chosen_fp64_state"): (32.06, 18.23, 2.04)}
+# The double-float state forms spend few FP64 instructions per sample and
+# are bound by instruction issue: one warp instruction per clock per
+# scheduler, 4 schedulers per SM, 152 SMs at 2.07 GHz = 1258.6 G warp-
+# instructions/s.  Their roofline: warp instructions issued per computed
+# sample (ncu smsp__inst_executed.sum over the computed samples of the
+# captured launch, same small cases as above) x computed samples over the
+# kernel's CUDA-event time, against that peak.
+ISSUE_PEAK_G = 152 * 4 * 2.07
+ISSUE_PER_SAMPLE = {("mba", "chosen"): 39.80, ("batched", "chosen"): 49.97,
+                    ("mba", "chosen_fp64_state"): 46.43}
+# DRAM bytes (read + write) of one stack launch on the small MBA case above
+# (200 exposures of 1024 x 1024, 512 orbits per family; BF16 planes 0.84 GB,
+# FP32 1.68 GB, both larger than L2), ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, with that case's algorithmic bytes (plane pairs of
+# the on-chip samples).  Family members read the same pixels, so traffic
+# grows more slowly than the orbit count: it is not scaled to the full
+# launch, whose own traffic stays null.
+TRAFFIC_SMALL_CASE = {("mba", "chosen"): (194741760, 343890136),
+                      ("mba", "chosen_fp64_state"): (142069504, 343890136),
+                      ("mba", "plain"): (177362176, 687780272),
+                      ("mba", "plain_fp64"): (177615104, 687780272)}
 
 
 def parse():
@@ -75,7 +96,7 @@ def parse():
                    help="image side (default 4096 for mba, 2048 for batched)")
     p.add_argument("--n-exp", type=int, default=200)
     p.add_argument("--plane", default="bf16", choices=["f32", "bf16", "f16"])
-    p.add_argument("--forms", default="chosen,plain,plain_fp64",
+    p.add_argument("--forms", default="chosen,chosen_fp64_state,plain,plain_fp64",
                    help="chosen (BF16, persistent, graph, vetting), plain (FP32 planes, one thread "
                         "per orbit), plain_fp64 (plain with FP64 light time and TAN projection)")
     p.add_argument("--no-e2e", action="store_true")
@@ -218,9 +239,9 @@ def make_workload(args, rank, device):
 
 
 class Form:
-    def __init__(self, name, plane, mode, graph, block=True, geom64=False):
+    def __init__(self, name, plane, mode, graph, block=True, geom64=False, df=False):
         self.name, self.plane, self.mode, self.graph, self.block = name, plane, mode, graph, block
-        self.geom64 = geom64
+        self.geom64, self.df = geom64, df
 
 
 NU_MIN = 5.0        # detection threshold of the candidate list (stacked SNR)
@@ -377,6 +398,9 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
     n = states.shape[1]
     ctx = ndt.create(device.index, stream)
     try:
+        ndt.set_block_test(ctx, form.block)
+        ndt.set_fp64_geometry(ctx, form.geom64)
+        ndt.set_df_state(ctx, form.df)
         tiles = None
         if form.mode == "persistent":
             if args.tiles:
@@ -391,8 +415,6 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
                 tiles = {"orbit_tile": ot, "exp_tile": et,
                          "sweep_ms": [round(float(t), 2) for t in times]}
             ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, ot, et, use_graph=form.graph)
-        ndt.set_block_test(ctx, form.block)
-        ndt.set_fp64_geometry(ctx, form.geom64)
         cand = Candidates(n, device, vet_params if form.name == "chosen" else None,
                           getattr(sky, "dedup_window", None))
         run_steps(ctx, stream, sky, imgs, states, args.warmup, form.plane, cand)
@@ -498,6 +520,9 @@ def bench_e2e(args, ctx, stream, sky, imgs, states, cand_dev, form, barrier, dev
     vet_params = cand_dev.vet_params
     try:
         for c in ctxs:
+            ndt.set_block_test(c, form.block)
+            ndt.set_fp64_geometry(c, form.geom64)
+            ndt.set_df_state(c, form.df)
             if form.mode == "persistent":
                 ndt.set_launch(c, ndt.LAUNCH_PERSISTENT, st["orbit_tile"], st["exp_tile"], use_graph=form.graph)
         cands = [Candidates(n, device, vet_params, cand_dev.window) for _ in range(2)]
@@ -671,32 +696,53 @@ def fp64_rates(device):
             for op in ("dfma", "dmul", "dadd")}
 
 
-def stack_roofline(workload, plane, res, rates):
-    """Roofline of the stack kernel: FP64-pipe instructions per computed sample
-    (ncu) x computed samples over the kernel's CUDA-event time, against the
-    measured DFMA issue rate; the instruction mix weighted by the measured
-    DFMA/DMUL/DADD rates gives the time bound the mix itself allows."""
+def stack_roofline(workload, form, plane, res, rates):
+    """Roofline of a stack kernel form.  FP64 state: FP64-pipe thread
+    instructions per computed sample (ncu, FP64_MIX) x computed samples over
+    the kernel's CUDA-event time, against the measured DFMA issue rate; the
+    mix weighted by the measured DFMA/DMUL/DADD rates gives the bound the mix
+    itself allows.  Double-float state: warp instructions issued per computed
+    sample (ISSUE_PER_SAMPLE) against the issue peak, with the FP64 pipe's
+    share beside it when its mix was measured."""
+    mix = FP64_MIX.get((workload, form))
+    issue = ISSUE_PER_SAMPLE.get((workload, form))
+    if mix is None and issue is None:
+        return None
     samples = res["samples"]
     stack_s = statistics.mean(res["stack_ms"]) / 1e3
-    flop, inst = FP64_PER_SAMPLE[workload]
-    n_fma, n_mul, n_add = FP64_MIX[workload]
-    computed = samples - res["skipped"]        # FP64 work runs only for these
-    gips = inst * computed / stack_s / 1e9
-    rest = inst - n_fma - n_mul - n_add        # conversions/compares: the DADD rate
-    mix_ns = n_fma / rates["dfma"] + (n_mul) / rates["dmul"] + (n_add + rest) / rates["dadd"]
-    peak_mix = inst / mix_ns
-    ach = flop * computed / stack_s / 1e12
-    return {"bound": "alu", "achieved": gips, "peak": rates["dfma"],
-            "unit": "G FP64-pipe thread-instructions/s", "frac": gips / rates["dfma"],
-            "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(workload),
-            "kernel": "stack kernel (FP64 pipe)",
-            "peak_source": "measured: DFMA chains at full occupancy (ndt_measure_fp64_rate)",
-            "peak_derived_from_unit_counts": FP64_PIPE_PEAK_GIPS,
-            "fp64_rates_measured_gips": rates,
-            "peak_for_this_mix": peak_mix, "frac_of_mix_peak": gips / peak_mix,
-            "fp64_pipe_inst_per_sample": inst, "fp64_mix_per_sample": FP64_MIX[workload],
-            "fp64_tflops": ach, "fp64_samples_per_launch": computed,
-            "algorithmic_bytes_per_launch": (8 if plane == "f32" else 4) * res["valid"]}
+    computed = samples - res["skipped"]        # the walk runs only for these
+    out = {"bound": "alu", "traffic": None, "fp64_samples_per_launch": computed,
+           "algorithmic_bytes_per_launch": (8 if plane == "f32" else 4) * res["valid"]}
+    small = TRAFFIC_SMALL_CASE.get((workload, form))
+    out["traffic_small_case"] = None if small is None else {
+        "bytes_per_launch": small[0], "algorithmic_bytes_per_launch": small[1],
+        "workload": "200 exposures 1024x1024, 512,000 orbits (1000 families)",
+        "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum"}
+    fp64 = None
+    if mix is not None:
+        n_fma, n_mul, n_add = mix
+        inst = n_fma + n_mul + n_add
+        gips = inst * computed / stack_s / 1e9
+        mix_ns = n_fma / rates["dfma"] + n_mul / rates["dmul"] + n_add / rates["dadd"]
+        peak_mix = inst / mix_ns
+        fp64 = {"achieved": gips, "peak": rates["dfma"], "unit": "G FP64-pipe thread-instructions/s",
+                "frac": gips / rates["dfma"],
+                "peak_source": "measured: DFMA chains at full occupancy (ndt_measure_fp64_rate)",
+                "peak_derived_from_unit_counts": FP64_PIPE_PEAK_GIPS,
+                "fp64_rates_measured_gips": rates,
+                "peak_for_this_mix": peak_mix, "frac_of_mix_peak": gips / peak_mix,
+                "fp64_inst_per_sample": inst, "fp64_mix_per_sample": mix,
+                "fp64_tflops": (2 * n_fma + n_mul + n_add) * computed / stack_s / 1e12}
+    if issue is None:
+        out.update(fp64)
+        out["kernel"] = f"stack kernel, {form} form (FP64 pipe)"
+        return out
+    g = issue * computed / stack_s / 1e9
+    out.update({"achieved": g, "peak": ISSUE_PEAK_G, "unit": "G warp-instructions issued/s",
+                "frac": g / ISSUE_PEAK_G, "kernel": f"stack kernel, {form} form (instruction issue)",
+                "peak_source": "unit counts: 1 warp instruction/clock x 4 schedulers x 152 SMs x 2.07 GHz",
+                "warp_inst_per_sample": issue, "fp64_pipe": fp64})
+    return out
 
 
 def form_record(res):
@@ -724,7 +770,11 @@ def e2e_record(e2e, samples, world, max_over_ranks):
             "candidate_list_equals_device": e2e["list_equals_device"]}
 
 
-DTYPE = "f64 state; df32 light time and TAN; bf16 planes; f32 sums"
+def form_dtype(form):
+    """The arithmetic the form's path computes in (not a precision claim)."""
+    state = ("df32 state (FP32 pairs; f64 for rare long steps)" if form.df else "f64 state")
+    geom = "f64 light time and TAN" if form.geom64 else "df32 light time and TAN"
+    return f"{state}; {geom}; {form.plane} planes; f32 sums"
 
 
 def batched_subrecord(args, rank, device, barrier, world, max_over_ranks, rates):
@@ -737,7 +787,7 @@ def batched_subrecord(args, rank, device, barrier, world, max_over_ranks, rates)
     b.workload, b.size, b.no_vet = "batched", 2048, True
     b.steps, b.warmup = min(args.steps, 5), 3
     sky, stream, imgs, states = make_workload(b, rank, device)
-    forms = {"chosen": Form("chosen", b.plane, "persistent", True),
+    forms = {"chosen": Form("chosen", b.plane, "persistent", True, df=True),
              "plain": Form("plain", "f32", "plain", False)}
     out = {"workload": workload_name(b, sky, states), "steps": b.steps, "warmup": b.warmup}
     res = {}
@@ -750,7 +800,7 @@ def batched_subrecord(args, rank, device, barrier, world, max_over_ranks, rates)
     r = res["chosen"]
     out["value"] = r["samples"] * world / max_over_ranks(statistics.mean(r["step_ms"]) / 1e3)
     out["unit"] = UNIT
-    out["roofline"] = stack_roofline("batched", b.plane, r, rates)
+    out["roofline"] = stack_roofline("batched", "chosen", b.plane, r, rates)
     del imgs, states
     torch.cuda.empty_cache()
     return out
@@ -768,8 +818,8 @@ def sparse_subrecord(args, rank, device, barrier, world, max_over_ranks, vet_par
     b.steps, b.warmup, b.tiles = min(args.steps, 3), 3, "128,16"
     b.no_e2e, b.vet_batch = True, 0
     sky, stream, imgs, states = make_workload(b, rank, device)
-    forms = [Form("chosen", b.plane, "persistent", True, block=True),
-             Form("chosen_without_block_test", b.plane, "persistent", True, block=False),
+    forms = [Form("chosen", b.plane, "persistent", True, block=True, df=True),
+             Form("chosen_without_block_test", b.plane, "persistent", True, block=False, df=True),
              Form("plain", "f32", "plain", False)]
     n = states.shape[1]
     out = {"workload": (f"sparse survey: {sky.ex.n} exposures {int(sky.ex.width[0])}^2 over a year, "
@@ -829,7 +879,8 @@ def main():
     sky, stream, imgs, states = make_workload(args, rank, device)
     forms = {"plain": Form("plain", "f32", "plain", False),
              "plain_fp64": Form("plain_fp64", "f32", "plain", False, geom64=True),
-             "chosen": Form("chosen", args.plane, "persistent", True)}
+             "chosen": Form("chosen", args.plane, "persistent", True, df=True),
+             "chosen_fp64_state": Form("chosen_fp64_state", args.plane, "persistent", True)}
     results, e2e = {}, None
     clocks = ClockSampler(local)
     clocks.start()
@@ -847,8 +898,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE if forms[head].plane == "bf16"
-        else DTYPE.replace("bf16", forms[head].plane), "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": form_dtype(forms[head]), "data": "synthetic",
         "config": {"workload": workload_name(args, sky, states),
                    "form": head, "planes": forms[head].plane,
                    "launch": forms[head].mode + ("+graph" if forms[head].graph else ""),
@@ -870,7 +920,10 @@ def main():
         line["vetting"] = vet_info
     for name, res in results.items():
         line[name] = form_record(res)
-    line["roofline"] = stack_roofline(args.workload, forms[head].plane, r, rates)
+        line[name]["roofline"] = stack_roofline(args.workload, name, forms[name].plane, res, rates)
+    line["roofline"] = line[head]["roofline"] or {"bound": "alu", "achieved": None, "peak": ISSUE_PEAK_G,
+                                                  "unit": "G warp-instructions issued/s", "frac": None,
+                                                  "traffic": None}
     if e2e is not None:
         line["e2e"] = e2e_record(e2e, samples, world, max_over_ranks)
     if rank == 0 and args.workload == "mba" and not args.no_noise:

@@ -257,6 +257,18 @@ ndt_status ndt_set_block_test(ndt_ctx *ctx, int32_t enabled);
    persistent form always uses the double-float geometry. */
 ndt_status ndt_set_fp64_geometry(ndt_ctx *ctx, int32_t enabled);
 
+/* Two-body state in double-float arithmetic (off by default): stack_orbits
+   (both forms) and predict_positions carry each orbit's position, velocity
+   and 1/|r| as FP32 pairs (~48 bits) through the short f and g series steps
+   (paper sec. 3, two-body motion about the Sun), instead of FP64; longer
+   steps still take the FP64 universal-variable solve.  On this GPU FP64
+   instructions retire at 1/64 of the FP32 rate, and with an FP64 state they
+   bound the stacking kernel.  Positions stay within ~1e-6 px of the FP64
+   state's at 0.2 arcsec pixels over hundreds of chained steps (sqrt(n)
+   2^-48 |r| of rounding noise).  With the double-float state the plain
+   form's FP64 geometry setting is ignored. */
+ndt_status ndt_set_df_state(ndt_ctx *ctx, int32_t enabled);
+
 /*
  * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}
  * and exp_tile in {8, 16, 32} on the given workload (arguments as for

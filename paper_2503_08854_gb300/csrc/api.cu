@@ -87,6 +87,7 @@ struct ndt_ctx {
   int32_t offchip = 1;     // off-chip test of the persistent form
   int32_t block_test = 1;  // warp cone test per exposure block (persistent form)
   int32_t geometry_fp64 = 0;  // plain form: FP64 light time and TAN projection
+  int32_t state_df = 0;    // two-body state in double-float (both forms and predict_positions)
   float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
@@ -150,7 +151,16 @@ void set_default_phys(ndt_ctx* c, double gm, double cl, double eps) {
   c->ph.inv_gm = gm > 0.0 ? 1.0 / gm : 0.0;
   c->ph.inv_c = cl > 0.0 ? (float)(1.0 / cl) : 0.0f;
   c->ph.inv_c2 = cl > 0.0 ? (float)(1.0 / (cl * cl)) : 0.0f;
-  c->ph.gm_f = gm > 0.0 ? (float)gm : 0.0f;
+  {
+    const dfloat g = split_df(gm > 0.0 ? gm : 0.0);
+    c->ph.gm_f = g.h;
+    c->ph.gm_l = g.l;
+    const dfloat sg = split_df(c->ph.sqrt_gm), isg = split_df(c->ph.inv_sqrt_gm);
+    c->ph.sgm_h = sg.h;
+    c->ph.sgm_l = sg.l;
+    c->ph.isgm_h = isg.h;
+    c->ph.isgm_l = isg.l;
+  }
   {
     const dfloat ic = split_df(cl > 0.0 ? 1.0 / cl : 0.0);
     c->ph.inv_c = ic.h;
@@ -405,7 +415,11 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     e.t = m.mjd;
     for (int i = 0; i < 3; ++i) e.obs[i] = m.obs_xyz[i];
     derive_projection(m, ctx->obliquity, e);
-    e.tf = (float)(m.mjd - ctx->t_ref);
+    {
+      const dfloat tt = split_df(m.mjd - ctx->t_ref);
+      e.tf = tt.h;
+      e.tf_l = tt.l;
+    }
     for (int i = 0; i < 3; ++i) {
       const dfloat o = split_df(m.obs_xyz[i]);
       e.obs_f[i] = o.h;
@@ -788,6 +802,7 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   a.offchip_test = persistent ? ctx->offchip : 0;
   a.block_test = persistent && ctx->offchip ? ctx->block_test : 0;
   a.geometry_fp64 = persistent ? 0 : ctx->geometry_fp64;
+  a.state_df = ctx->state_df;
   s = run_stack(ctx, a);
   if (s != NDT_OK) return s;
   ctx->last_n = n_orbits;
@@ -870,8 +885,8 @@ ndt_status ndt_predict_positions(ndt_ctx* ctx, const double* states, double t0, 
     dst = ctx->xy_tmp.as<double>();
   }
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_predict(static_cast<const double*>(st_dev), n_orbits, t0, ctx->ex_dev.as<ExpDev>(),
-                        ctx->pos_to_table_dev.as<int32_t>(), ctx->n_exp, ctx->ph, dst,
+  NDT_CK(launch_predict(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref, ctx->ex_dev.as<ExpDev>(),
+                        ctx->pos_to_table_dev.as<int32_t>(), ctx->n_exp, ctx->ph, ctx->state_df != 0, dst,
                         ctx->counters.as<unsigned long long>(), ctx->stream), "predict kernel");
   ctx->launches += 1;
   if (host_out) NDT_CK(cudaMemcpyAsync(xy_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->stream), "D2H");
@@ -936,6 +951,12 @@ ndt_status ndt_set_offchip_test(ndt_ctx* ctx, int32_t enabled) {
 ndt_status ndt_set_fp64_geometry(ndt_ctx* ctx, int32_t enabled) {
   if (!ctx) return NDT_EINVAL;
   ctx->geometry_fp64 = enabled ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_set_df_state(ndt_ctx* ctx, int32_t enabled) {
+  if (!ctx) return NDT_EINVAL;
+  ctx->state_df = enabled ? 1 : 0;
   return NDT_OK;
 }
 

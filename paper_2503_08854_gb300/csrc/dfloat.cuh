@@ -144,6 +144,25 @@ NDT_HD dfloat df_add(dfloat a, dfloat b) {
   return fast_two_sum(s.h, add_rn(s.l, add_rn(a.l, b.l)));
 }
 
+NDT_HD dfloat df_neg(dfloat a) { return {-a.h, -a.l}; }
+
+NDT_HD dfloat df_sub(dfloat a, dfloat b) { return df_add(a, df_neg(b)); }
+
+// a + b for an FP32 b
+NDT_HD dfloat df_add_f(dfloat a, float b) {
+  const dfloat s = two_sum(a.h, b);
+  return fast_two_sum(s.h, add_rn(s.l, a.l));
+}
+
+// a b for an FP32 b; relative error ~2^-47
+NDT_HD dfloat df_mul_f(dfloat a, float b) {
+  const dfloat p = two_prod(a.h, b);
+  return fast_two_sum(p.h, fma_rn(a.l, b, p.l));
+}
+
+// a 2^k (s = 2^k): exact
+NDT_HD dfloat df_scale2(dfloat a, float s) { return {mul_rn(a.h, s), mul_rn(a.l, s)}; }
+
 // floor(hi + lo) for a normalised pair: floor(hi), one lower when hi is an
 // integer and lo < 0; INT_MIN when |hi| >= 2^30 or not finite
 NDT_HD int df_floor(dfloat x) {

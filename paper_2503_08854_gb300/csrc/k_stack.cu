@@ -11,6 +11,8 @@
 // statistic is formed in the epilogue.  The FP64 pipe bounds this kernel;
 // the gathers move 8 bytes (FP32 planes) or 4 bytes (BF16/FP16) per valid
 // sample.
+#include <type_traits>
+
 #include "ndt_internal.cuh"
 
 namespace ndt {
@@ -25,6 +27,12 @@ constexpr int kBlock = 128;
 // survey, 1.9 % on the batched one.  6 spills ~170 bytes.
 #ifndef NDT_STACK_MINB
 #define NDT_STACK_MINB 5
+#endif
+// The double-float walk fits in 72 registers without spilling (no FP64
+// state): 7 x 128 threads per SM, 28 warps, 1.6-4 % faster than 5 or 6 on the
+// main-belt survey; 8 spills.
+#ifndef NDT_STACK_MINB_DF
+#define NDT_STACK_MINB_DF 8
 #endif
 
 __device__ __forceinline__ void load_state(const double* __restrict__ s, int64_t n, int64_t o,
@@ -45,17 +53,44 @@ __device__ __forceinline__ int64_t upper_bound_i64(const int64_t* __restrict__ a
   return lo;
 }
 
-// Per-thread walk state.
-struct Walk {
-  double r[3], v[3], rn, inv_r, t_prev;
+// Per-thread walk state: what every form carries (orbit constants, sums,
+// counts) and the two-body state, in FP64 (Walk) or double-float (WalkDF).
+struct WalkBase {
   OrbitConst oc;
   CSum sp, sf;
   int cnt;
   int skipped;         // samples whose FP64 work the off-chip test removed
   int blocked;         // of which the block cone test removed
   bool failed;
+};
+
+struct Walk : WalkBase {
+  double r[3], v[3], rn, inv_r, t_prev;
   float rf[3], vf[3], tf;   // FP32 copy of the state and its epoch (off-chip test)
 };
+
+struct WalkDF : WalkBase {
+  StateDF s;
+  dfloat tp;           // epoch of the state - t_ref
+};
+
+// FP32 view of the state and its epoch (- t_ref) for the off-chip and block tests
+__device__ __forceinline__ void fp32_view(const Walk& w, float rf[3], float vf[3], float& tf) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    rf[i] = w.rf[i];
+    vf[i] = w.vf[i];
+  }
+  tf = w.tf;
+}
+__device__ __forceinline__ void fp32_view(const WalkDF& w, float rf[3], float vf[3], float& tf) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    rf[i] = w.s.r[i].h;
+    vf[i] = w.s.v[i].h;
+  }
+  tf = w.tp.h;
+}
 
 __device__ __forceinline__ void walk_fp32_copy(Walk& w, float tf) {
 #pragma unroll
@@ -66,6 +101,15 @@ __device__ __forceinline__ void walk_fp32_copy(Walk& w, float tf) {
   w.tf = tf;
 }
 
+__device__ __forceinline__ void walk_base_init(WalkBase& w) {
+  w.sp = CSum{0.0f, 0.0f};
+  w.sf = CSum{0.0f, 0.0f};
+  w.cnt = 0;
+  w.skipped = 0;
+  w.blocked = 0;
+  w.failed = false;
+}
+
 __device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double* __restrict__ states,
                                           int64_t n, int64_t o, double t0, double t_ref = 0.0) {
   load_state(states, n, o, w.r, w.v);
@@ -73,21 +117,34 @@ __device__ __forceinline__ void walk_init(Walk& w, const Phys& ph, const double*
   w.inv_r = 1.0 / w.rn;
   w.oc = orbit_const(ph, w.r, w.v, w.inv_r);
   w.t_prev = t0;
-  w.sp = CSum{0.0f, 0.0f};
-  w.sf = CSum{0.0f, 0.0f};
-  w.cnt = 0;
-  w.skipped = 0;
-  w.blocked = 0;
-  w.failed = false;
+  walk_base_init(w);
   walk_fp32_copy(w, (float)(t0 - t_ref));
+}
+
+__device__ __forceinline__ void walk_init(WalkDF& w, const Phys& ph, const double* __restrict__ states,
+                                          int64_t n, int64_t o, double t0, double t_ref) {
+  double r[3], v[3];
+  load_state(states, n, o, r, v);
+  const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  const double inv_r = 1.0 / rn;
+  w.oc = orbit_const(ph, r, v, inv_r);
+  w.s = state_df(r, v, rn, inv_r);
+  w.tp = split_df(t0 - t_ref);
+  walk_base_init(w);
 }
 
 // Persistent form: before the FP64 step, the warp skips the sample when the
 // FP32 off-chip test holds for every lane (lanes without work vote yes); the
 // state then stays at its last epoch and the next computed step is longer.
 // Every lane of the warp must call this (the vote is warp-wide).
-__device__ __forceinline__ bool warp_skips(Walk& w, const Phys& ph, const ExpDev& e, bool active) {
-  const bool off = !active || w.failed || certainly_off_chip(ph, w.oc, w.rf, w.vf, w.tf, e);
+template <class W>
+__device__ __forceinline__ bool warp_skips(W& w, const Phys& ph, const ExpDev& e, bool active) {
+  bool off = !active || w.failed;
+  if (!off) {
+    float rf[3], vf[3], tf;
+    fp32_view(w, rf, vf, tf);
+    off = certainly_off_chip(ph, w.oc, rf, vf, tf, e);
+  }
   if (!__all_sync(0xffffffffu, off)) return false;
   if (active && !w.failed) w.skipped += 1;
   return true;
@@ -102,7 +159,8 @@ __device__ __forceinline__ bool warp_skips(Walk& w, const Phys& ph, const ExpDev
 // warp's centre and its tangent point exceeds the warp radius plus the chip
 // cone's radius; lane jj tests exposure jj and a ballot gives the mask.
 // Warp-uniform; every lane must call it.
-__device__ __forceinline__ unsigned warp_block_mask(const Walk& w, const Phys& ph, const ExpDev* blk, int cnt,
+template <class W>
+__device__ __forceinline__ unsigned warp_block_mask(const W& w, const Phys& ph, const ExpDev* blk, int cnt,
                                                     bool active) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -121,7 +179,11 @@ __device__ __forceinline__ unsigned warp_block_mask(const Walk& w, const Phys& p
   const unsigned act = __ballot_sync(full, has);
   if (act == 0u) return all;                   // no orbit of this warp needs any sample
   float u[3] = {0.0f, 0.0f, 0.0f}, ang = 0.0f;
-  if (has) ang = block_direction(ph, w.oc, w.rf, w.vf, w.tf, tm, h, om, d, u);
+  if (has) {
+    float rf[3], vf[3], tf;
+    fp32_view(w, rf, vf, tf);
+    ang = block_direction(ph, w.oc, rf, vf, tf, tm, h, om, d, u);
+  }
   const int lead = __ffs(act) - 1;
   const float c[3] = {__shfl_sync(full, u[0], lead), __shfl_sync(full, u[1], lead),
                       __shfl_sync(full, u[2], lead)};
@@ -184,7 +246,31 @@ __device__ __forceinline__ void walk_sample(Walk& w, const Phys& ph, const ExpDe
   }
 }
 
-__device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, int64_t o,
+// The double-float walk: step, light time and projection without FP64
+// instructions (the FP32 view of the state is its high parts).
+template <int PT, bool FP32_COPY = false, bool GEOM64 = false>
+__device__ __forceinline__ void walk_sample(WalkDF& w, const Phys& ph, const ExpDev& e,
+                                            const void* __restrict__ planes) {
+  static_assert(!GEOM64, "the double-float walk has no FP64 geometry");
+  if (w.failed) return;
+  const dfloat te = {e.tf, e.tf_l};
+  if (kepler_step_df(ph, w.oc, df_sub(te, w.tp), w.s) < 0) {
+    w.failed = true;
+    return;
+  }
+  w.tp = te;
+  dfloat rho[3];
+  apparent_rho_dfs(ph, w.s.r, w.s.v, w.s.ir.h, e, rho);
+  int ix, iy;
+  if (pixel_of(e, rho, ix, iy)) {
+    const float2 pv = gather_plane<PT>(planes, e, ix, iy);
+    w.sp.add(pv.x);
+    w.sf.add(pv.y);
+    w.cnt += 1;
+  }
+}
+
+__device__ __forceinline__ void walk_finish(const WalkBase& w, const StackArgs& a, int64_t o,
                                             bool active) {
   int valid = 0, fails = 0, skipped = 0, blocked = 0;
   if (active) {
@@ -215,14 +301,18 @@ __device__ __forceinline__ void walk_finish(const Walk& w, const StackArgs& a, i
   }
 }
 
-// Plain form: one thread per orbit, grid covers all orbits.
-template <int PT, bool GEOM64>
-__global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const StackArgs a) {
+// Plain form: one thread per orbit, grid covers all orbits.  GEOM: 0 FP64
+// state, double-float light time and projection; 1 FP64 throughout; 2
+// double-float state (WalkDF).
+template <int PT, int GEOM>
+__global__ void __launch_bounds__(kBlock, GEOM == 2 ? NDT_STACK_MINB_DF : NDT_STACK_MINB)
+    k_stack_plain(const StackArgs a) {
+  using W = typename std::conditional<GEOM == 2, WalkDF, Walk>::type;
   const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   const bool active = o < a.n;
-  Walk w;
+  W w;
   if (active) {
-    walk_init(w, a.ph, a.states, a.n, o, a.t0);
+    walk_init(w, a.ph, a.states, a.n, o, a.t0, a.t_ref);
     int64_t e_begin = 0, e_end = a.n_exp;
     if (a.n_fam > 0) {
       const int64_t f = upper_bound_i64(a.fam_orb_off, a.n_fam + 1, o) - 1;
@@ -231,7 +321,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_plain(const St
     }
     for (int64_t k = e_begin; k < e_end; ++k) {
       const int j = a.n_fam > 0 ? __ldg(a.fam_exp_pos + k) : (int)k;
-      walk_sample<PT, false, GEOM64>(w, a.ph, a.ex[j], a.planes);
+      walk_sample<PT, false, GEOM == 1>(w, a.ph, a.ex[j], a.planes);
     }
   }
   walk_finish(w, a, o, active);
@@ -259,8 +349,10 @@ __device__ __forceinline__ void team_sync(int team) {
 // exposure records at a time in shared memory and walks its orbits through
 // them.  The loop ends when the counter passes the last item: no thread ever
 // waits on another team.
-template <int PT, int TEAM_WARPS, int ET>
-__global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(const StackArgs a) {
+template <int PT, int TEAM_WARPS, int ET, bool DFS>
+__global__ void __launch_bounds__(kBlock, DFS ? NDT_STACK_MINB_DF : NDT_STACK_MINB)
+    k_stack_persistent(const StackArgs a) {
+  using W = typename std::conditional<DFS, WalkDF, Walk>::type;
   constexpr int TEAM = TEAM_WARPS * 32;
   constexpr int NTEAMS = kBlock / TEAM;
   __shared__ ExpDev stage[NTEAMS][ET];
@@ -279,7 +371,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
     const int64_t o = o_begin + tile * TEAM + tl;
     const bool active = o < o_end;
     const int64_t e_begin = __ldg(a.fam_exp_off + f), e_end = __ldg(a.fam_exp_off + f + 1);
-    Walk w;
+    W w;
     if (active) {
       walk_init(w, a.ph, a.states, a.n, o, a.t0, a.t_ref);
     } else {
@@ -311,6 +403,7 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
         }
       }
       // every lane runs the loop: the off-chip vote is warp-wide
+#pragma unroll 1
       for (int jj = 0; jj < cnt; ++jj) {
         const ExpDev& e = stage[team][jj];
         if ((miss >> jj) & 1u) {
@@ -330,27 +423,43 @@ __global__ void __launch_bounds__(kBlock, NDT_STACK_MINB) k_stack_persistent(con
   }
 }
 
+// One step of a walk to exposure e and its topocentric vector; false when
+// the step failed.
+__device__ __forceinline__ bool walk_step_rho(Walk& w, const Phys& ph, const ExpDev& e, dfloat rd[3]) {
+  if (kepler_step(ph, w.oc, e.t - w.t_prev, w.r, w.v, w.rn, w.inv_r) < 0) return false;
+  w.t_prev = e.t;
+  apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rd);
+  return true;
+}
+__device__ __forceinline__ bool walk_step_rho(WalkDF& w, const Phys& ph, const ExpDev& e, dfloat rd[3]) {
+  const dfloat te = {e.tf, e.tf_l};
+  if (kepler_step_df(ph, w.oc, df_sub(te, w.tp), w.s) < 0) return false;
+  w.tp = te;
+  apparent_rho_dfs(ph, w.s.r, w.s.v, w.s.ir.h, e, rd);
+  return true;
+}
+
+template <bool DFS>
 __global__ void __launch_bounds__(kBlock) k_predict(const double* __restrict__ states, int64_t n,
-                                                   double t0, const ExpDev* __restrict__ ex,
+                                                   double t0, double t_ref, const ExpDev* __restrict__ ex,
                                                    const int32_t* __restrict__ pos_to_table,
                                                    int32_t n_exp, Phys ph, double* __restrict__ xy,
                                                    unsigned long long* counters) {
+  using W = typename std::conditional<DFS, WalkDF, Walk>::type;
   const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
   if (o >= n) return;
-  Walk w;
-  walk_init(w, ph, states, n, o, t0);
+  W w;
+  walk_init(w, ph, states, n, o, t0, t_ref);
   for (int j = 0; j < n_exp; ++j) {
     const ExpDev& e = ex[j];
     double* out = xy + ((size_t)o * n_exp + pos_to_table[j]) * 2;
     double x = __longlong_as_double(0x7ff8000000000000ll), y = x;
     if (!w.failed) {
-      if (kepler_step(ph, w.oc, e.t - w.t_prev, w.r, w.v, w.rn, w.inv_r) < 0) {
+      dfloat rd[3];
+      if (!walk_step_rho(w, ph, e, rd)) {
         w.failed = true;
         atomicAdd(counters + 1, 1ull);
       } else {
-        w.t_prev = e.t;
-        dfloat rd[3];
-        apparent_rho_df(ph, w.r, w.v, w.inv_r, e, rd);
         const double rho[3] = {f2d_exact(rd[0].h) + f2d_exact(rd[0].l), f2d_exact(rd[1].h) + f2d_exact(rd[1].l),
                                f2d_exact(rd[2].h) + f2d_exact(rd[2].l)};
         double px, py;
@@ -362,17 +471,17 @@ __global__ void __launch_bounds__(kBlock) k_predict(const double* __restrict__ s
   }
 }
 
-template <int PT>
+template <int PT, bool DFS>
 cudaError_t launch_persistent_pt(const StackArgs& a, int n_sms, cudaStream_t st) {
   // one wave: as many resident CTAs per SM as registers and shared memory allow
 #define NDT_CASE(TW, ET)                                                         \
   if (a.orbit_tile == TW * 32 && a.exp_tile == ET) {                             \
     int per_sm = 0;                                                              \
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(               \
-        &per_sm, k_stack_persistent<PT, TW, ET>, kBlock, 0);                     \
+        &per_sm, k_stack_persistent<PT, TW, ET, DFS>, kBlock, 0);                \
     if (e != cudaSuccess) return e;                                              \
     const int blocks = n_sms * (per_sm > 0 ? per_sm : 1);                        \
-    k_stack_persistent<PT, TW, ET><<<blocks, kBlock, 0, st>>>(a);                \
+    k_stack_persistent<PT, TW, ET, DFS><<<blocks, kBlock, 0, st>>>(a);           \
     return cudaGetLastError();                                                   \
   }
   NDT_CASE(1, 8) NDT_CASE(1, 16) NDT_CASE(1, 32)
@@ -382,36 +491,46 @@ cudaError_t launch_persistent_pt(const StackArgs& a, int n_sms, cudaStream_t st)
   return cudaErrorInvalidValue;
 }
 
+template <int GEOM>
+void launch_plain_geom(const StackArgs& a, unsigned blocks, cudaStream_t st) {
+  if (a.plane_type == kF32) k_stack_plain<kF32, GEOM><<<blocks, kBlock, 0, st>>>(a);
+  else if (a.plane_type == kBF16) k_stack_plain<kBF16, GEOM><<<blocks, kBlock, 0, st>>>(a);
+  else k_stack_plain<kF16, GEOM><<<blocks, kBlock, 0, st>>>(a);
+}
+
 }  // namespace
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st) {
   const int64_t blocks = (a.n + kBlock - 1) / kBlock;
   if (blocks == 0) return cudaSuccess;
-  if (a.geometry_fp64) {
-    if (a.plane_type == kF32) k_stack_plain<kF32, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-    else if (a.plane_type == kBF16) k_stack_plain<kBF16, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-    else k_stack_plain<kF16, true><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-  } else {
-    if (a.plane_type == kF32) k_stack_plain<kF32, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-    else if (a.plane_type == kBF16) k_stack_plain<kBF16, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-    else k_stack_plain<kF16, false><<<(unsigned)blocks, kBlock, 0, st>>>(a);
-  }
+  if (a.state_df) launch_plain_geom<2>(a, (unsigned)blocks, st);
+  else if (a.geometry_fp64) launch_plain_geom<1>(a, (unsigned)blocks, st);
+  else launch_plain_geom<0>(a, (unsigned)blocks, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st) {
-  if (a.plane_type == kF32) return launch_persistent_pt<kF32>(a, n_sms, st);
-  if (a.plane_type == kBF16) return launch_persistent_pt<kBF16>(a, n_sms, st);
-  return launch_persistent_pt<kF16>(a, n_sms, st);
+  if (a.state_df) {
+    if (a.plane_type == kF32) return launch_persistent_pt<kF32, true>(a, n_sms, st);
+    if (a.plane_type == kBF16) return launch_persistent_pt<kBF16, true>(a, n_sms, st);
+    return launch_persistent_pt<kF16, true>(a, n_sms, st);
+  }
+  if (a.plane_type == kF32) return launch_persistent_pt<kF32, false>(a, n_sms, st);
+  if (a.plane_type == kBF16) return launch_persistent_pt<kBF16, false>(a, n_sms, st);
+  return launch_persistent_pt<kF16, false>(a, n_sms, st);
 }
 
-cudaError_t launch_predict(const double* states, int64_t n, double t0, const ExpDev* ex,
-                           const int32_t* pos_to_table, int32_t n_exp, Phys ph, double* xy,
-                           unsigned long long* counters, cudaStream_t st) {
+cudaError_t launch_predict(const double* states, int64_t n, double t0, double t_ref, const ExpDev* ex,
+                           const int32_t* pos_to_table, int32_t n_exp, Phys ph, bool state_df,
+                           double* xy, unsigned long long* counters, cudaStream_t st) {
   const int64_t blocks = (n + kBlock - 1) / kBlock;
   if (blocks == 0) return cudaSuccess;
-  k_predict<<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, ex, pos_to_table, n_exp, ph, xy,
-                                                counters);
+  if (state_df)
+    k_predict<true><<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, t_ref, ex, pos_to_table, n_exp, ph,
+                                                         xy, counters);
+  else
+    k_predict<false><<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, t_ref, ex, pos_to_table, n_exp, ph,
+                                                          xy, counters);
   return cudaGetLastError();
 }
 

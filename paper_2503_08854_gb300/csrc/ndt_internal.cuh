@@ -49,8 +49,10 @@ struct ExpDev {
   float p0_l[3], ax_l[3], ay_l[3], crh_h[2], crh_l[2];
   float obs_l[3];    // low parts of obs (high parts: obs_f), for the double-float light time
   float chip_sin;    // sin of the chip cone's radius
+  float tf_l;        // epoch - t_ref - tf: the epoch as the double-float pair (tf, tf_l)
+  int32_t pad_;
 };
-static_assert(sizeof(ExpDev) == 288 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
+static_assert(sizeof(ExpDev) == 296 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
@@ -63,6 +65,10 @@ struct Phys {
   int32_t force_free;
   float inv_c_l;    // 1/c - inv_c: 1/c as the double-float pair (inv_c, inv_c_l)
   float inv_c3;     // 1 / c^3
+  float gm_l;       // GM_sun - gm_f: GM_sun as the double-float pair (gm_f, gm_l)
+  float sgm_h, sgm_l;     // sqrt(GM_sun) as a double-float pair
+  float isgm_h, isgm_l;   // 1 / sqrt(GM_sun) as a double-float pair
+  int32_t pad_;
 };
 
 // Plane storage type tags.
@@ -136,6 +142,26 @@ __device__ __forceinline__ void stumpff_series(double z, double& C, double& S) {
   S = s;
 }
 
+// Closed forms for |z| >= 1.5 (long steps of fast or long-period orbits):
+// out of line, so that their library calls stay out of the instruction
+// stream of the short steps.
+static __device__ __noinline__ double2 stumpff_closed(double z) {
+  double C, S;
+  if (z > 0.0) {
+    double q = sqrt(z), sn, cs;
+    sincos(q, &sn, &cs);
+    C = (1.0 - cs) / z;
+    S = (q - sn) / (z * q);
+  } else {
+    double q = sqrt(-z);
+    double e = exp(q), ei = 1.0 / e;
+    double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
+    C = (ch - 1.0) / (-z);
+    S = (sh - q) / ((-z) * q);
+  }
+  return make_double2(C, S);
+}
+
 __device__ __forceinline__ void stumpff(double z, double& C, double& S) {
   // tier choice by an FP32 compare (every boundary has a wide margin)
   const float zf = d2f_trunc(z), az = fabsf(zf);
@@ -149,17 +175,10 @@ __device__ __forceinline__ void stumpff(double z, double& C, double& S) {
     stumpff_series<8>(z, C, S);
   } else if (az < 1.5f) {
     stumpff_series<11>(z, C, S);
-  } else if (zf > 0.0f) {
-    double q = sqrt(z), sn, cs;
-    sincos(q, &sn, &cs);
-    C = (1.0 - cs) / z;
-    S = (q - sn) / (z * q);
   } else {
-    double q = sqrt(-z);
-    double e = exp(q), ei = 1.0 / e;
-    double ch = 0.5 * (e + ei), sh = 0.5 * (e - ei);
-    C = (ch - 1.0) / (-z);
-    S = (sh - q) / ((-z) * q);
+    const double2 cs = stumpff_closed(z);
+    C = cs.x;
+    S = cs.y;
   }
 }
 
@@ -184,8 +203,10 @@ struct OrbitConst {
   float jerk6, half_acc, vq;
 };
 
-__device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
-                                                  const double v[3], double inv_r) {
+// (out of line: once per orbit and tile, its divisions and roots would
+// otherwise sit in the instruction stream of the walk)
+static __device__ __noinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
+                                                      const double v[3], double inv_r) {
   OrbitConst oc;
   double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   oc.alpha = 2.0 * inv_r - v2 * ph.inv_gm;
@@ -444,6 +465,251 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
 }
 
 // ---------------------------------------------------------------------------
+// The two-body state in double-float arithmetic (FP32 pairs, ~48 bits).
+//
+// On this GPU the FP64 pipe retires 1/64 of the FP32 rate, and with an FP64
+// state the short steps above spend ~39 FP64 instructions per sample, which
+// bound the stacking kernel.  Carried as double-float pairs, the same f and g
+// series take ~450 FP32 instructions, about 7 FP64 instructions' worth of
+// issue time.  Every term keeps the precision the FP64 step gives it (the
+// FP32 parts stay FP32, the FP64 parts become double-float); what changes is
+// the rounding unit of the state and of those parts, 2^-48 instead of 2^-53.
+// Over n chained steps that adds about sqrt(n) 2^-48 |r| of rounding noise
+// to the position (1e-13 AU after 300 steps at 3 AU): 1e-7 px at 0.2 arcsec
+// pixels for a main-belt orbit, 1e-6 px for an NEO 0.05 AU away.  Steps
+// beyond the series' range (the universal-variable solve, force-free motion)
+// convert the state to FP64, take the FP64 step and convert back: they are
+// one step per night, not one per sample.
+// ---------------------------------------------------------------------------
+struct StateDF {
+  dfloat r[3], v[3];
+  dfloat ir;   // 1 / |r|
+  float rn;    // |r| (FP32: it only enters FP32 terms)
+};
+
+__device__ __forceinline__ StateDF state_df(const double r[3], const double v[3], double rn, double inv_r) {
+  StateDF s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    s.r[i] = split_df(r[i]);
+    s.v[i] = split_df(v[i]);
+  }
+  s.ir = split_df(inv_r);
+  s.rn = d2f_rn(rn);
+  return s;
+}
+
+// R + (a R + b V), a and b double-float coefficients of the two-body update
+__device__ __forceinline__ dfloat df_update(dfloat R, dfloat a, dfloat b, dfloat V) {
+  return df_add(R, df_add(df_mul(a, R), df_mul(b, V)));
+}
+
+// fg_series_step with the state, u, p, t^2 and the FP64 parts in double-float,
+// and one order more, so that it holds for dt^2 K <= 1e-6 (sqrt(10) times the
+// FP64 series' range: 0.1-0.2 day for main-belt orbits, the gaps between
+// visits of a night).  With f_n, g_n the coefficients of the Lagrange series
+// (f_{n+1} = f_n' - u g_n, g_{n+1} = f_n + g_n', u' = -3 u p, p' = w - 2 p^2,
+// w' = -p (u + 2 w)):
+//   f_5 = 15 p u (7 p^2 - 3 w - u),   g_5 = -u (45 p^2 - 9 w - u),
+//   f_6 = -u (945 p^4 - 630 p^2 w - 210 p^2 u + 45 w^2 + 24 w u + u^2),
+//   g_6 = 30 p u (14 p^2 - 6 w - u).
+// f and g gain f_5 t^5/120 and g_5 t^5/120, fdot and gdot f_5 t^4/24 +
+// f_6 t^5/120 and g_5 t^4/24 + g_6 t^5/120.  With |u|, p^2, |w| <= K the sum
+// of |coefficients| of f_n is 2.58 K^3 n! at n = 6 and 5.06 K^3.5 n! at n = 7,
+// so at dt^2 K <= 1e-6 the neglected terms are below 3e-18 of f, 1e-15 of
+// g - t and 5e-17 of the velocity: under the 2^-48 rounding of the state.
+// Every new term is below 1e-8 of the quantity it corrects: FP32.
+__device__ __forceinline__ void fg_series_step_df(const Phys& ph, const OrbitConst& oc, dfloat t, StateDF& s) {
+  const dfloat ir2 = df_mul(s.ir, s.ir);
+  const dfloat u = df_mul(df_mul(dfloat{ph.gm_f, ph.gm_l}, ir2), s.ir);
+  const dfloat p = df_mul(df_dot3(s.r, s.v), ir2);
+  const dfloat t2 = df_mul(t, t);
+  const dfloat A = df_scale2(df_mul(u, t2), -0.5f);                     // -u t^2 / 2
+  // FP32 parts, as in fg_series_step
+  const float tf = t.h, uf = u.h, pf = p.h;
+  const float wf = uf * fmaf(-oc.alpha_f, s.rn, 1.0f);
+  const float c4f = uf * fmaf(3.0f, wf, fmaf(-15.0f * pf, pf, uf));
+  const float upf = uf * pf;
+  const float t2f = tf * tf, t3f = t2f * tf, t4f = t2f * t2f, t5f = t4f * tf;
+  const float p2f = pf * pf;
+  const float f5 = 15.0f * upf * (7.0f * p2f - 3.0f * wf - uf);
+  const float g5 = -uf * (45.0f * p2f - 9.0f * wf - uf);
+  const float f6 = -uf * (p2f * (945.0f * p2f - 630.0f * wf - 210.0f * uf) + wf * (45.0f * wf + 24.0f * uf) +
+                          uf * uf);
+  const float g6 = 30.0f * upf * (14.0f * p2f - 6.0f * wf - uf);
+  const float Bf = fmaf(0.5f * upf, t3f, fmaf(c4f * (1.0f / 24.0f), t4f, f5 * (1.0f / 120.0f) * t5f));
+  const float Gf = fmaf(-uf * (1.0f / 6.0f), t3f, fmaf(0.25f * upf, t4f, g5 * (1.0f / 120.0f) * t5f));
+  const float Kf = fmaf(c4f * (1.0f / 6.0f), t3f, fmaf(f5 * (1.0f / 24.0f), t4f, f6 * (1.0f / 120.0f) * t5f));
+  const float Lf = fmaf(upf, t3f, fmaf(g5 * (1.0f / 24.0f), t4f, g6 * (1.0f / 120.0f) * t5f));
+  // double-float parts
+  const dfloat fm1 = df_add_f(A, Bf);
+  const dfloat g = df_add_f(t, Gf);
+  const dfloat fdot = df_sub(df_add_f(df_mul(df_mul_f(df_mul(u, p), 1.5f), t2), Kf), df_mul(u, t));
+  const dfloat gdm1 = df_add_f(A, Lf);
+  dfloat rr[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) rr[i] = df_update(s.r[i], fm1, g, s.v[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.v[i] = df_update(s.v[i], gdm1, fdot, s.r[i]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
+  // 1/|r|: y0 = (1/r)(1 - p t), e = 1 - x y0^2 (|e| = O(dt^2 K) <= 1e-6),
+  // y = y0 (1 + e/2 + 3 e^2/8), remainder 5 e^3 / 16 < 1e-18
+  const dfloat x = df_dot3(s.r, s.r);
+  const dfloat y0 = df_sub(s.ir, df_mul(s.ir, df_mul(p, t)));
+  const dfloat e = df_add_f(df_neg(df_mul(x, df_mul(y0, y0))), 1.0f);
+  const dfloat c = df_add_f(df_scale2(e, 0.5f), 0.375f * e.h * e.h);
+  s.ir = df_add(y0, df_mul(y0, c));
+  s.rn = x.h * s.ir.h;
+}
+
+// fg_tiny_step with the state, u and the FP64 parts in double-float
+__device__ __forceinline__ void fg_tiny_step_df(const Phys& ph, const OrbitConst& oc, dfloat t, StateDF& s) {
+  const dfloat ir2 = df_mul(s.ir, s.ir);
+  const dfloat u = df_mul(df_mul(dfloat{ph.gm_f, ph.gm_l}, ir2), s.ir);
+  const float irf = s.ir.h, tf = t.h, uf = u.h;
+  const float rvf = fmaf(s.r[0].h, s.v[0].h, fmaf(s.r[1].h, s.v[1].h, s.r[2].h * s.v[2].h));
+  const float pf = rvf * irf * irf;
+  const float upf = uf * pf;
+  const float t2f = tf * tf, t3f = t2f * tf;
+  const float Af = -0.5f * uf * t2f;
+  const float fm1f = fmaf(0.5f * upf, t3f, Af);
+  const float gm1f = -uf * (1.0f / 6.0f) * t3f;
+  const float wf = uf * fmaf(-oc.alpha_f, s.rn, 1.0f);
+  const float c4f = uf * fmaf(3.0f, wf, fmaf(-15.0f * pf, pf, uf));
+  const float kf = fmaf(1.5f * upf, t2f, (c4f * (1.0f / 6.0f)) * t3f);
+  const float gdm1f = fmaf(upf, t3f, Af);
+  const dfloat g = df_add_f(t, gm1f);
+  const dfloat fdot = df_add_f(df_neg(df_mul(u, t)), kf);
+  dfloat rr[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    rr[i] = df_add(s.r[i], df_add(df_mul_f(s.r[i], fm1f), df_mul(g, s.v[i])));
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    s.v[i] = df_add(s.v[i], df_add(df_mul_f(s.v[i], gdm1f), df_mul(fdot, s.r[i])));
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
+  const dfloat x = df_dot3(s.r, s.r);
+  const dfloat y0 = df_add(s.ir, df_mul_f(s.ir, -pf * tf));
+  const dfloat e = df_add_f(df_neg(df_mul(x, df_mul(y0, y0))), 1.0f);
+  s.ir = df_add(y0, df_mul(y0, df_scale2(e, 0.5f)));
+  s.rn = x.h * s.ir.h;
+}
+
+// A step the series do not cover, through FP64: the state is widened (each
+// pair summed in FP64), stepped by kepler_step and split again.
+static __device__ __noinline__ int kepler_step_df_long(const Phys& ph, const OrbitConst& oc, dfloat dt, StateDF& s) {
+  double r[3], v[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    r[i] = f2d_exact(s.r[i].h) + f2d_exact(s.r[i].l);
+    v[i] = f2d_exact(s.v[i].h) + f2d_exact(s.v[i].l);
+  }
+  double inv_r = f2d_exact(s.ir.h) + f2d_exact(s.ir.l);
+  double rn = (r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) * inv_r;
+  const int it = kepler_step(ph, oc, f2d_exact(dt.h) + f2d_exact(dt.l), r, v, rn, inv_r);
+  s = state_df(r, v, rn, inv_r);
+  return it;
+}
+
+// The universal-variable step of kepler_step in double-float, for steps
+// beyond the series' range with |z| = |alpha chi^2| <= 1e-2 (a day for a
+// main-belt orbit, z ~ 2e-5; a few days for an NEO).  F, F' and the outputs
+// are double-float; the Stumpff functions are 1/2 - z/24 and 1/6 - z/120 in
+// double-float plus the z^2 and z^3 terms in FP32 (below 1.4e-7, rounded to
+// 1e-14; the neglected z^4 terms are below 3e-15), which keeps chi to
+// ~1e-16 and the position to the state's rounding.  The Laguerre-Conway
+// correction delta, F'' and the stopping test are FP32 as in kepler_step,
+// and the outputs are taken at chi - delta to first order.  Returns the
+// number of evaluations, or 0 with the state untouched when |z| leaves the
+// range or 4 evaluations do not converge: the caller then takes the FP64
+// step.
+constexpr float kInv6h = (float)(1.0 / 6.0), kInv6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
+constexpr float kInv24h = (float)(1.0 / 24.0), kInv24l = (float)(1.0 / 24.0 - (double)(float)(1.0 / 24.0));
+constexpr float kInv120h = (float)(1.0 / 120.0),
+                kInv120l = (float)(1.0 / 120.0 - (double)(float)(1.0 / 120.0));
+
+__device__ __forceinline__ int kepler_uv_df(const Phys& ph, const OrbitConst& oc, dfloat dt, StateDF& s) {
+  const dfloat r0 = df_mul(df_dot3(s.r, s.r), s.ir);
+  const dfloat sig0 = df_mul(df_dot3(s.r, s.v), dfloat{ph.isgm_h, ph.isgm_l});
+  const dfloat al = split_df(oc.alpha);
+  const dfloat a1 = df_add_f(df_neg(df_mul(al, r0)), 1.0f);      // 1 - alpha r0
+  const dfloat sdt = df_mul(dfloat{ph.sgm_h, ph.sgm_l}, dt);
+  // third-order series guess of chi(dt), as in kepler_step
+  const float irf = s.ir.h, uf = sdt.h * irf, sif = sig0.h * irf;
+  const float chif =
+      uf * fmaf(uf, fmaf(-uf * (1.0f / 6.0f), fmaf(-3.0f * sif, sif, irf - oc.alpha_f), -0.5f * sif), 1.0f);
+  if (!(fabsf(oc.alpha_f) * chif * chif <= 5e-3f)) return 0;
+  dfloat chi = {chif, 0.0f};
+#pragma unroll 1
+  for (int it = 1; it <= 4; ++it) {
+    const dfloat chi2 = df_mul(chi, chi);
+    const dfloat z = df_mul(al, chi2);
+    const float zf = z.h;
+    if (!(fabsf(zf) <= 1e-2f)) return 0;
+    const float tc = zf * zf * fmaf(-zf, 1.0f / 40320.0f, 1.0f / 720.0f);
+    const float ts = zf * zf * fmaf(-zf, 1.0f / 362880.0f, 1.0f / 5040.0f);
+    const dfloat C = df_add_f(df_add_f(df_mul(z, dfloat{-kInv24h, -kInv24l}), tc), 0.5f);
+    const dfloat S = df_add(df_add_f(df_mul(z, dfloat{-kInv120h, -kInv120l}), ts), dfloat{kInv6h, kInv6l});
+    const dfloat chi2C = df_mul(chi2, C);
+    const dfloat chi3S = df_mul(df_mul(chi2, chi), S);
+    const dfloat chi1mzS = df_mul(chi, df_add_f(df_neg(df_mul(z, S)), 1.0f));   // chi (1 - z S)
+    const float omzCf = fmaf(-zf, C.h, 1.0f);                                     // 1 - z C
+    const dfloat F = df_add(df_add(df_mul(sig0, chi2C), df_mul(a1, chi3S)), df_sub(df_mul(r0, chi), sdt));
+    const dfloat dF = df_add(df_add(df_mul(sig0, chi1mzS), df_mul(a1, chi2C)), r0);   // = |r|
+    const float d2Ff = fmaf(sig0.h, omzCf, a1.h * chi1mzS.h);
+    const float Ff = F.h, dFf = dF.h;
+    const float disc = fabsf(16.0f * dFf * dFf - 20.0f * Ff * d2Ff);
+    const float delta = 5.0f * Ff / (dFf + sqrtf(disc));
+    if (fabsf(delta) <= kKeplerStop) {
+      // outputs at chi - delta, to first order in delta
+      const dfloat chi2C_c = df_sub(chi2C, df_mul_f(chi1mzS, delta));
+      const dfloat fm1 = df_neg(df_mul(chi2C_c, s.ir));                               // f - 1
+      const dfloat g = df_sub(dt, df_mul(df_sub(chi3S, df_mul_f(chi2C, delta)), dfloat{ph.isgm_h, ph.isgm_l}));
+      const dfloat rc = df_add_f(dF, -delta * d2Ff);
+      const dfloat inv_rc = df_div(dfloat{1.0f, 0.0f}, rc);
+      const dfloat fdot = df_neg(df_mul(df_mul(dfloat{ph.sgm_h, ph.sgm_l}, df_add_f(chi1mzS, -delta * omzCf)),
+                                        df_mul(inv_rc, s.ir)));
+      const dfloat gdm1 = df_neg(df_mul(chi2C_c, inv_rc));                           // gdot - 1
+      dfloat rr[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) rr[i] = df_update(s.r[i], fm1, g, s.v[i]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s.v[i] = df_update(s.v[i], gdm1, fdot, s.r[i]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
+      s.ir = inv_rc;
+      s.rn = rc.h;
+      return it;
+    }
+    chi = df_add_f(chi, -delta);
+  }
+  return 0;
+}
+
+// kepler_step for the double-float state: the series steps in double-float
+// (fg_series_step_df up to dt^2 K <= 1e-6, i.e. sqrt(10) times the FP64
+// series bound), then the double-float universal-variable step where |z| <=
+// 1e-2, every other step through FP64.  Returns as kepler_step does.
+__device__ __forceinline__ int kepler_step_df(const Phys& ph, const OrbitConst& oc, dfloat dt, StateDF& s) {
+  const float adtf = fabsf(dt.h);   // within 2^-24 of |dt|: inside the 1e-6 shrink of the bounds
+  // (3.1622775 < sqrt(10); its product's rounding stays inside the 1e-6 shrink)
+  if (!ph.force_free && adtf <= oc.series_dt_f * 3.1622775f) {
+    if (adtf <= oc.tiny_dt_f)
+      fg_tiny_step_df(ph, oc, dt, s);
+    else
+      fg_series_step_df(ph, oc, dt, s);
+    return 0;
+  }
+  if (!ph.force_free && adtf <= oc.half_period_f) {
+    const int it = kepler_uv_df(ph, oc, dt, s);
+    if (it > 0) return it;
+  }
+  return kepler_step_df_long(ph, oc, dt, s);
+}
+
+// ---------------------------------------------------------------------------
 // Light-time corrected topocentric vector, in double-float arithmetic (FP32
 // pairs, ~48 bits; see dfloat.cuh).  With (r, v) the geometric state at the
 // exposure epoch, u = GM/|r|^3, p = (r.v)/|r|^2 and d = r - r_obs, the
@@ -462,22 +728,14 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
 // (tau to ~1e-14 relative), the small terms FP32, and the state enters
 // through the integer-pipe split of its FP64 values: no FP64 instruction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void apparent_rho_df(const Phys& ph, const double r[3], const double v[3],
-                                                double inv_r, const ExpDev& e, dfloat rho[3]) {
-  dfloat R[3];
+__device__ __forceinline__ void apparent_rho_dfs(const Phys& ph, const dfloat R[3], const dfloat V[3],
+                                                 float irf, const ExpDev& e, dfloat rho[3]) {
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    R[i] = split_df(r[i]);
-    rho[i] = df_add(R[i], {-e.obs_f[i], -e.obs_l[i]});     // d
-  }
+  for (int i = 0; i < 3; ++i) rho[i] = df_add(R[i], {-e.obs_f[i], -e.obs_l[i]});     // d
   if (ph.inv_c == 0.0f) return;
-  dfloat V[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) V[i] = split_df(v[i]);
   const dfloat dist = df_sqrt(df_dot3(rho, rho));
   const float dv = fmaf(rho[0].h, V[0].h, fmaf(rho[1].h, V[1].h, rho[2].h * V[2].h));
   const float v2 = fmaf(V[0].h, V[0].h, fmaf(V[1].h, V[1].h, V[2].h * V[2].h));
-  const float irf = d2f_rn(inv_r);
   const float uf = ph.force_free ? 0.0f : ph.gm_f * irf * irf * irf;
   const float dr = fmaf(rho[0].h, R[0].h, fmaf(rho[1].h, R[1].h, rho[2].h * R[2].h));
   const float pf = fmaf(R[0].h, V[0].h, fmaf(R[1].h, V[1].h, R[2].h * V[2].h)) * irf * irf;
@@ -492,6 +750,18 @@ __device__ __forceinline__ void apparent_rho_df(const Phys& ph, const double r[3
     const float small = fmaf(hf, R[i].h, kf * fmaf(-3.0f * pf, R[i].h, V[i].h));
     rho[i] = df_add(df_add(rho[i], {-tv.h, -tv.l}), {small, 0.0f});
   }
+}
+
+// The same from an FP64 state (split into pairs on the integer pipe).
+__device__ __forceinline__ void apparent_rho_df(const Phys& ph, const double r[3], const double v[3],
+                                                double inv_r, const ExpDev& e, dfloat rho[3]) {
+  dfloat R[3], V[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R[i] = split_df(r[i]);
+    V[i] = split_df(v[i]);
+  }
+  apparent_rho_dfs(ph, R, V, d2f_rn(inv_r), e, rho);
 }
 
 // The same light-time model in FP64 throughout (the all-FP64 geometry of
@@ -729,12 +999,13 @@ struct StackArgs {
   int32_t offchip_test;        // persistent form: skip FP64 work of certainly off-chip samples
   int32_t block_test;          // persistent form: warp cone test per staged exposure block
   int32_t geometry_fp64;       // plain form: FP64 light time and TAN projection
+  int32_t state_df;            // two-body state in double-float (WalkDF) instead of FP64
 };
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);
 cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st);
-cudaError_t launch_predict(const double* states, int64_t n, double t0, const ExpDev* ex,
-                           const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph,
+cudaError_t launch_predict(const double* states, int64_t n, double t0, double t_ref, const ExpDev* ex,
+                           const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph, bool state_df,
                            double* xy, unsigned long long* counters, cudaStream_t st);
 
 // Number of values of nu (n of them) at least thr, into *out (device).

@@ -135,6 +135,142 @@ def _tiny(r, v, t, inv_r, alpha):
     return rr, vv, _fma(0.5 * y0, e, y0)
 
 
+def _series_df(r, v, t, inv_r, alpha):
+    """The double-float state's series step (Delta t^2 K <= 1e-6, one order
+    more than _series) with its double-float parts exact (40 digits: their
+    2^-48 rounding is the state's, bounded separately) and its FP32 parts in
+    FP32, as the kernel forms them."""
+    R = [mp.mpf(x) for x in r]
+    V = [mp.mpf(x) for x in v]
+    T = mp.mpf(t)
+    ir = mp.mpf(inv_r)
+    ir2 = ir * ir
+    u = mp.mpf(GM) * ir2 * ir
+    p = sum(R[i] * V[i] for i in range(3)) * ir2
+    a = -u * T * T / 2
+    tf, uf, pf = f32(t), f32(float(u)), f32(float(p))
+    wf = uf * (f32(1.0) - f32(alpha) * f32(1.0 / inv_r))
+    c4 = uf * (f32(3.0) * wf + (f32(-15.0) * pf) * pf + uf)
+    upf = uf * pf
+    p2 = pf * pf
+    t2f = tf * tf
+    t3f, t4f = t2f * tf, t2f * t2f
+    t5f = t4f * tf
+    f5 = f32(15.0) * upf * (f32(7.0) * p2 - f32(3.0) * wf - uf)
+    g5 = -uf * (f32(45.0) * p2 - f32(9.0) * wf - uf)
+    f6 = -uf * (p2 * (f32(945.0) * p2 - f32(630.0) * wf - f32(210.0) * uf) + wf * (f32(45.0) * wf + f32(24.0) * uf)
+                + uf * uf)
+    g6 = f32(30.0) * upf * (f32(14.0) * p2 - f32(6.0) * wf - uf)
+    bf = f32(0.5) * upf * t3f + c4 * f32(1 / 24) * t4f + f5 * f32(1 / 120) * t5f
+    gf = -uf * f32(1 / 6) * t3f + f32(0.25) * upf * t4f + g5 * f32(1 / 120) * t5f
+    kf = c4 * f32(1 / 6) * t3f + f5 * f32(1 / 24) * t4f + f6 * f32(1 / 120) * t5f
+    lf = upf * t3f + g5 * f32(1 / 24) * t4f + g6 * f32(1 / 120) * t5f
+    fm1 = a + mp.mpf(float(bf))
+    g = T + mp.mpf(float(gf))
+    fdot = 3 * u * p / 2 * T * T + mp.mpf(float(kf)) - u * T
+    gdm1 = a + mp.mpf(float(lf))
+    rr = [R[i] + fm1 * R[i] + g * V[i] for i in range(3)]
+    vv = [V[i] + gdm1 * V[i] + fdot * R[i] for i in range(3)]
+    x = sum(q * q for q in rr)
+    y0 = ir - ir * (p * T)
+    e = 1 - x * y0 * y0
+    y = y0 + y0 * (e / 2 + mp.mpf(float(f32(0.375) * f32(float(e)) * f32(float(e)))))
+    return rr, vv, y
+
+
+def _uv_df(r, v, t, inv_r, alpha):
+    """The double-float universal-variable step (|z| <= 1e-2) as the kernel
+    forms it: double-float quantities exact (40 digits), FP32 parts FP32.
+    Returns None where the kernel hands the step to FP64."""
+    R = [mp.mpf(x) for x in r]
+    V = [mp.mpf(x) for x in v]
+    T = mp.mpf(t)
+    ir = mp.mpf(inv_r)
+    sgm = mp.sqrt(mp.mpf(GM))
+    r0 = sum(x * x for x in R) * ir
+    sig0 = sum(R[i] * V[i] for i in range(3)) / sgm
+    al = mp.mpf(alpha)
+    a1 = 1 - al * r0
+    sdt = sgm * T
+    irf, alf = f32(inv_r), f32(alpha)
+    uf, sif = f32(float(sdt)) * irf, f32(float(sig0)) * irf
+    chif = uf * (uf * ((-uf * f32(1 / 6)) * (f32(-3.0) * sif * sif + (irf - alf)) + f32(-0.5) * sif) + f32(1.0))
+    if not abs(alf) * chif * chif <= f32(5e-3):
+        return None
+    chi = mp.mpf(float(chif))
+    for _ in range(4):
+        chi2 = chi * chi
+        z = al * chi2
+        zf = f32(float(z))
+        if not abs(zf) <= f32(1e-2):
+            return None
+        tc = zf * zf * (-zf * f32(1 / 40320) + f32(1 / 720))
+        ts = zf * zf * (-zf * f32(1 / 362880) + f32(1 / 5040))
+        C = -z / 24 + mp.mpf(float(tc)) + mp.mpf(1) / 2
+        S = -z / 120 + mp.mpf(float(ts)) + mp.mpf(1) / 6
+        chi2c, chi3s = chi2 * C, chi2 * chi * S
+        chi1mzs = chi * (1 - z * S)
+        omzcf = f32(1.0) - zf * f32(float(C))
+        F = sig0 * chi2c + a1 * chi3s + r0 * chi - sdt
+        dF = sig0 * chi1mzs + a1 * chi2c + r0
+        d2f = f32(float(sig0)) * omzcf + f32(float(a1)) * f32(float(chi1mzs))
+        ff, dff = f32(float(F)), f32(float(dF))
+        disc = abs(f32(16.0) * dff * dff - f32(20.0) * ff * d2f)
+        delta = f32(5.0) * ff / (dff + np.sqrt(disc))
+        if abs(delta) <= f32(1e-7):
+            d = mp.mpf(float(delta))
+            chi2c_c = chi2c - chi1mzs * d
+            fm1 = -chi2c_c * ir
+            g = T - (chi3s - chi2c * d) / sgm
+            rc = dF + mp.mpf(float(-delta * d2f))
+            inv_rc = 1 / rc
+            fdot = -sgm * (chi1mzs + mp.mpf(float(-delta * omzcf))) * inv_rc * ir
+            gdm1 = -chi2c_c * inv_rc
+            rr = [R[i] + fm1 * R[i] + g * V[i] for i in range(3)]
+            vv = [V[i] + gdm1 * V[i] + fdot * R[i] for i in range(3)]
+            return rr, vv, inv_rc
+        chi -= mp.mpf(float(delta))
+    return None
+
+
+def test_double_float_universal_variable_step():
+    """The double-float universal-variable step on NEO, main-belt and Kuiper-
+    belt conics, steps from the end of the series' range (dt^2 K = 1e-6) to
+    |z| near 1e-2: position to 2e-15 and velocity to 5e-15 relative (the
+    first-order correction at chi - delta leaves (delta^2/2) |f''| r0 with
+    delta <= 1e-7), and every step accepted for |z| <= 5e-3."""
+    rng = np.random.default_rng(29)
+    worst = dict(pos=0.0, vel=0.0, inv_r=0.0)
+    n = 0
+    for kind in ("neo", "mba", "tno"):
+        for _ in range(8):
+            r, v = _conic(rng, kind)
+            k, alpha = _bound_k(r, v)
+            rn = float(np.linalg.norm(r))
+            t_lo = math.sqrt(1e-6 / k)
+            t_hi = 0.07 * rn ** 1.5 / math.sqrt(GM) / math.sqrt(max(abs(alpha) * rn, 1e-3))
+            for t in (t_lo * 1.01, math.sqrt(t_lo * t_hi), t_hi):
+                t *= rng.choice([-1.0, 1.0])
+                inv_r = float(1 / mp.sqrt(sum(mp.mpf(x) ** 2 for x in r)))
+                got = _uv_df(list(r), list(v), t, inv_r, alpha)
+                z_est = abs(alpha) * (math.sqrt(GM) * t / rn) ** 2
+                if got is None:
+                    assert z_est > 4e-3, (kind, t, z_est)
+                    continue
+                n += 1
+                rr, vv, y = got
+                re, ve = _exact_step(r, v, t)
+                rabs = float(mp.sqrt(sum(x * x for x in re)))
+                vabs = float(mp.sqrt(sum(x * x for x in ve)))
+                worst["pos"] = max(worst["pos"], max(abs(float(rr[i] - re[i])) for i in range(3)) / rabs)
+                worst["vel"] = max(worst["vel"], max(abs(float(vv[i] - ve[i])) for i in range(3)) / vabs)
+                rnew = mp.sqrt(sum(mp.mpf(x) ** 2 for x in re))
+                worst["inv_r"] = max(worst["inv_r"], abs(float(y * rnew - 1)))
+    print("uv_df", n, {k: f"{w:.2e}" for k, w in worst.items()})
+    assert n >= 40
+    assert worst["pos"] <= 2e-15 and worst["vel"] <= 5e-15 and worst["inv_r"] <= 1e-15
+
+
 def _conic(rng, kind):
     rmag, ecc = {"neo": (rng.uniform(0.7, 1.5), rng.uniform(0.2, 0.9)),
                  "mba": (rng.uniform(2.0, 3.5), rng.uniform(0.0, 0.3)),
@@ -159,9 +295,10 @@ def _bound_k(r, v):
 # the shortest tier is at rounding (without its c4 t^3/6 term in fdot,
 # whose one-sided error would drift the velocity, it reaches ~4.4e-16)
 @pytest.mark.parametrize("tier,bound,step,vel_tol", [("series", 1e-7, _series, 8e-16),
-                                                     ("tiny", 3e-10, _tiny, 3e-16)])
+                                                     ("tiny", 3e-10, _tiny, 3e-16),
+                                                     ("series_df", 1e-6, _series_df, 1e-16)])
 def test_short_step_tiers_at_fp64_rounding(tier, bound, step, vel_tol):
-    rng = np.random.default_rng(17 if tier == "series" else 5)
+    rng = np.random.default_rng({"series": 17, "tiny": 5, "series_df": 23}[tier])
     worst = dict(pos=0.0, vel=0.0, inv_r=0.0)
     for kind in ("neo", "mba", "tno", "hyp"):
         for frac in (1.0, 0.3):
