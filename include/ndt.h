@@ -251,22 +251,25 @@ ndt_status ndt_set_block_test(ndt_ctx *ctx, int32_t enabled);
 
 /* All-FP64 geometry for the plain form (off by default): light time and the
    TAN projection of stack_orbits in FP64 instead of double-float (FP32
-   pairs), with the nearest pixel from an FP64 floor; the propagated state is
-   FP64 in both.  The reference-precision variant the faster default is
-   measured against (positions agree to ~1e-7 px at 0.2 arcsec pixels).  The
-   persistent form always uses the double-float geometry. */
+   pairs), with the nearest pixel from an FP64 floor.  Takes effect with the
+   FP64 state (ndt_set_df_state(ctx, 0)).  The reference-precision variant
+   the faster forms are measured against (positions agree to ~1e-7 px at 0.2
+   arcsec pixels).  The persistent form always uses the double-float
+   geometry. */
 ndt_status ndt_set_fp64_geometry(ndt_ctx *ctx, int32_t enabled);
 
-/* Two-body state in double-float arithmetic (off by default): stack_orbits
-   (both forms) and predict_positions carry each orbit's position, velocity
-   and 1/|r| as FP32 pairs (~48 bits) through the short f and g series steps
-   (paper sec. 3, two-body motion about the Sun), instead of FP64; longer
-   steps still take the FP64 universal-variable solve.  On this GPU FP64
-   instructions retire at 1/64 of the FP32 rate, and with an FP64 state they
-   bound the stacking kernel.  Positions stay within ~1e-6 px of the FP64
-   state's at 0.2 arcsec pixels over hundreds of chained steps (sqrt(n)
-   2^-48 |r| of rounding noise).  With the double-float state the plain
-   form's FP64 geometry setting is ignored. */
+/* Two-body state in double-float arithmetic (on by default; enabled = 0
+   selects the FP64 state): stack_orbits (both forms) and predict_positions
+   carry each orbit's position, velocity and 1/|r| as FP32 pairs (~48 bits)
+   through the f and g series steps (to dt^2 K <= 1e-6, one order beyond the
+   FP64 series) and the universal-variable step where |alpha chi^2| <= 1e-2
+   (paper sec. 3, two-body motion about the Sun); other steps convert to
+   FP64, step and convert back.  On this GPU FP64 instructions retire at 1/64
+   of the FP32 rate, and with an FP64 state they bound the stacking kernel.
+   Positions stay within ~1e-6 px of the FP64 state's at 0.2 arcsec pixels
+   over hundreds of chained steps (sqrt(n) 2^-48 |r| of rounding noise).
+   With the double-float state the plain form's FP64 geometry setting is
+   ignored. */
 ndt_status ndt_set_df_state(ndt_ctx *ctx, int32_t enabled);
 
 /*

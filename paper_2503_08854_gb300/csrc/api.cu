@@ -87,7 +87,7 @@ struct ndt_ctx {
   int32_t offchip = 1;     // off-chip test of the persistent form
   int32_t block_test = 1;  // warp cone test per exposure block (persistent form)
   int32_t geometry_fp64 = 0;  // plain form: FP64 light time and TAN projection
-  int32_t state_df = 0;    // two-body state in double-float (both forms and predict_positions)
+  int32_t state_df = 1;    // two-body state in double-float (both forms and predict_positions)
   float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
@@ -475,6 +475,17 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
   if (any_host_img) NDT_CK(ctx->stage_images.ensure(sizeof(float) * img_elems), "image staging");
   if (any_host_var) NDT_CK(ctx->stage_vars.ensure(sizeof(float) * img_elems), "variance staging");
   int64_t img_off = 0;
+  // host images that follow each other in memory (in epoch order) go over in
+  // one copy: a run [run_src, run_src + run_bytes) to run_dst
+  const char* run_src = nullptr;
+  char* run_dst = nullptr;
+  size_t run_bytes = 0;
+  auto flush_run = [&]() -> cudaError_t {
+    cudaError_t e = cudaSuccess;
+    if (run_bytes) e = cudaMemcpyAsync(run_dst, run_src, run_bytes, cudaMemcpyHostToDevice, ctx->stream);
+    run_bytes = 0;
+    return e;
+  };
   for (int s = 0; s < n_exp; ++s) {
     const int j = ctx->sorted_to_table[s];
     const size_t bytes = sizeof(float) * (size_t)meta[j].width * meta[j].height;
@@ -483,7 +494,13 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
       J.image = images[j];
     } else {
       float* dst = ctx->stage_images.as<float>() + img_off;
-      NDT_CK(cudaMemcpyAsync(dst, images[j], bytes, cudaMemcpyHostToDevice, ctx->stream), "image H2D");
+      const char* src = reinterpret_cast<const char*>(images[j]);
+      if (!(run_bytes && src == run_src + run_bytes && reinterpret_cast<char*>(dst) == run_dst + run_bytes)) {
+        NDT_CK(flush_run(), "image H2D");
+        run_src = src;
+        run_dst = reinterpret_cast<char*>(dst);
+      }
+      run_bytes += bytes;
       J.image = dst;
     }
     J.var = nullptr;
@@ -499,6 +516,7 @@ ndt_status ndt_load_exposures(ndt_ctx* ctx, const ndt_exposure* meta, int32_t n_
     }
     img_off += (int64_t)meta[j].width * meta[j].height;
   }
+  NDT_CK(flush_run(), "image H2D");
   // exposures without a variance (<= 0, no variance planes): iterative MAD
   ctx->noise_sigma.assign(n_exp, 0.0f);
   if (!variances) {

@@ -313,8 +313,9 @@ def set_fp64_geometry(ctx, enabled=True):
 
 
 def set_df_state(ctx, enabled=True):
-    """ndt_set_df_state: the two-body state in double-float (FP32 pairs)
-    instead of FP64, in both stack forms and predict_positions."""
+    """ndt_set_df_state: the two-body state in double-float (FP32 pairs, the
+    default) or, with enabled=False, in FP64, in both stack forms and
+    predict_positions."""
     _check(ctx, _lib.ndt_set_df_state(ctx, 1 if enabled else 0))
 
 

@@ -290,6 +290,7 @@ def test_fp64_geometry_form_matches_oracle(gpu):
     gpu.load(sky.ex, imgs)
     pl = [O.planes(imgs[j], sky.ex.sigma[j], sky.ex.var[j]) for j in range(sky.ex.n)]
     ref = O.stack(sky.states, sky.t0, sky.ex, planes=([p[0] for p in pl], [p[1] for p in pl]))
+    ndt.set_df_state(gpu.ctx, False)     # the FP64 geometry goes with the FP64 state
     ndt.set_fp64_geometry(gpu.ctx, True)
     out64 = gpu.stack(sky.states, sky.t0)
     check_stack(out64, ref)
