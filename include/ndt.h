@@ -98,8 +98,9 @@ typedef struct {
   int32_t exp_tile;
   int32_t launch_mode;
   int32_t plane_dtype;
-  int64_t offchip_skipped;   /* samples of the last stack whose FP64 work the
-                                off-chip test removed (persistent form)     */
+  int64_t offchip_skipped;   /* samples of the last stack whose step, light
+                                time and projection the off-chip test
+                                removed (persistent form)                   */
   int64_t block_skipped;     /* of which the block cone test removed         */
 } ndt_stats;
 
@@ -161,10 +162,10 @@ ndt_status ndt_load_exposures(ndt_ctx *ctx, const ndt_exposure *meta, int32_t n_
  * Outputs (each n_orbits long; any may be NULL): psi_sum, phi_sum (FP32),
  * nobs (int32), snr (FP32).  The per-orbit nu always stays in the context
  * for ndt_topk_candidates.  Sums are accumulated in FP32 with compensation.
- * The propagated state is FP64 (the shortest steps' small terms in FP32);
- * light time and projection are double-float (FP32 pairs, ~48 bits), which
- * keeps pixel coordinates within ~1e-7 px of an all-FP64 evaluation at
- * 0.2 arcsec pixels.
+ * The propagated state is double-float (FP32 pairs, ~48 bits; see
+ * ndt_set_df_state) or FP64; light time and projection are double-float,
+ * which keeps pixel coordinates within ~1e-7 px of an all-FP64 evaluation
+ * at 0.2 arcsec pixels.
  */
 ndt_status ndt_stack_orbits(ndt_ctx *ctx, const double *states, double t0, int64_t n_orbits,
                             const int64_t *fam_orbit_off, const int64_t *fam_exp_off,
@@ -222,7 +223,7 @@ ndt_status ndt_set_launch(ndt_ctx *ctx, int32_t mode, int32_t orbit_tile, int32_
 ndt_status ndt_set_filter_broadening(ndt_ctx *ctx, float sigma_px);
 
 /* Off-chip test of the persistent form (on by default; the plain form never
-   uses it).  Before the FP64 step of a sample, an FP32 second-order
+   uses it).  Before the two-body step of a sample, an FP32 second-order
    prediction of its pixel with a rigorous error bound (Taylor remainder from
    the orbit's perihelion jerk bound, light time, FP32 rounding, TAN stretch)
    is compared with the image; when every lane of a warp is certainly off
@@ -238,7 +239,7 @@ ndt_status ndt_set_offchip_test(ndt_ctx *ctx, int32_t enabled);
    exp_tile records a team walks at a time, in epoch order) each warp bounds
    the sky directions its orbits can take during the block by one cone: each
    orbit's direction at the block's middle epoch, predicted in FP32 from its
-   last FP64 state, widened by the rigorous error bound of the off-chip test,
+   last computed state, widened by the rigorous error bound of the off-chip test,
    the motion over the block and the spread of the block's observer
    positions.  Exposures whose chip cone (tangent point, largest off-axis
    angle + 0.01 rad) lies outside the warp's cone are skipped by the whole
@@ -441,8 +442,8 @@ ndt_status ndt_topk_noalloc(const float *snr_dev, int64_t n, int64_t k, int64_t 
                             float *snr_out, void *cuda_stream);
 
 /* Measured issue rate of the FP64 pipe on `device` (no counterpart in the
-   paper; the denominator of the stacking kernel's roofline, which is bound
-   by FP64 instructions).  op 0 = DFMA, 1 = DMUL, 2 = DADD: every thread of a
+   paper; the denominator of the FP64-state stacking kernel's roofline,
+   which is bound by FP64 instructions).  op 0 = DFMA, 1 = DMUL, 2 = DADD: every thread of a
    full-occupancy grid runs eight independent chains of that instruction;
    *inst_per_s = thread-instructions retired per second over four launches
    (after one warm-up launch), *seconds (may be NULL) = their duration.

@@ -1074,7 +1074,7 @@ ndt_status make_stamps(ndt_ctx* ctx, const double* states, double t0, int64_t n_
   int* pos_cnt = reinterpret_cast<int*>(ctx->stamp_pos.as<int2>() + n_cand * ctx->n_exp);
   // reset the failure counter only: the valid-sample count of the last stack stays
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref,
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref, ctx->state_df != 0,
                                 static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
                                 ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(), pos_cnt,
                                 ctx->counters.as<unsigned long long>(), ctx->stream), "stamp positions");
@@ -1133,7 +1133,8 @@ ndt_status ndt_dedup_candidates(ndt_ctx* ctx, const double* states, double t0, i
   int* n_keep_dev = reinterpret_cast<int*>(static_cast<unsigned char*>(ctx->dedup_ref.p) +
                                            ((sizeof(int32_t) * nr + 3) / 4) * 4);
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_dedup(static_cast<const double*>(st_dev), n_orbits, t0, static_cast<const int64_t*>(cd),
+  NDT_CK(launch_dedup(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref, ctx->state_df != 0,
+                         static_cast<const int64_t*>(cd),
                       n_cand, ctx->ex_dev.as<ExpDev>(), ctx->dedup_ref.as<int32_t>(), nr, ctx->ph, radius_px,
                       ctx->dedup_scratch.p, ctx->counters.as<unsigned long long>(), out, n_keep_dev,
                       ctx->stream),
@@ -1246,7 +1247,7 @@ ndt_status ndt_trim_candidates(ndt_ctx* ctx, const double* states, double t0, in
   int* pos_cnt = reinterpret_cast<int*>(ctx->stamp_pos.as<int2>() + n_cand * ctx->n_exp);
   NDT_CK(ctx->trim_bits.ensure(4 * trim_scratch_words(n_cand, ctx->n_exp)), "trim scratch");
   NDT_CK(cudaMemsetAsync(ctx->counters.as<unsigned long long>() + 1, 0, 8, ctx->stream), "memset");
-  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref,
+  NDT_CK(launch_stamp_positions(static_cast<const double*>(st_dev), n_orbits, t0, ctx->t_ref, ctx->state_df != 0,
                                 static_cast<const int64_t*>(cd), n_cand, ctx->ex_dev.as<ExpDev>(),
                                 ctx->n_exp, ctx->ph, ctx->stamp_pos.as<int2>(), pos_cnt,
                                 ctx->counters.as<unsigned long long>(), ctx->stream), "trim positions");

@@ -9,8 +9,8 @@
 // their rank order (a local-maximum rule in track space).
 //
 // Positions come from the same propagation, light time and double-float TAN
-// projection as the stack (chained universal-variable steps through the
-// reference epochs).  Neighbours are found through a hash grid over the
+// projection as the stack (chained two-body steps through the reference
+// epochs, in the stack's state arithmetic).  Neighbours are found through a hash grid over the
 // positions at the first and last reference exposures (four coordinates;
 // the middle one alone when n_ref = 1) with cells of size 2r: a track within
 // r of candidate i lies, in each coordinate, in i's cell or in the adjacent
@@ -55,11 +55,13 @@ __device__ __forceinline__ bool pixel_xy_df(const ExpDev& e, const dfloat R[3], 
 // Positions of every candidate at the reference exposures (sorted positions
 // ref[0] < ref[1] < ... in epoch order): P[i * n_ref + k], NaN where the
 // tangent point is 90 degrees or more away or the candidate index is out of
-// range.
+// range.  DFS: the double-float state (as the stack's default), else FP64.
+template <bool DFS>
 __global__ void __launch_bounds__(kDedupThreads)
-    k_track_ref(const double* __restrict__ states, int64_t n, double t0, const int64_t* __restrict__ cand,
-                int64_t n_cand, const ExpDev* __restrict__ ex, const int32_t* __restrict__ ref, int n_ref,
-                Phys ph, float2* __restrict__ P, unsigned long long* counters) {
+    k_track_ref(const double* __restrict__ states, int64_t n, double t0, double t_ref,
+                const int64_t* __restrict__ cand, int64_t n_cand, const ExpDev* __restrict__ ex,
+                const int32_t* __restrict__ ref, int n_ref, Phys ph, float2* __restrict__ P,
+                unsigned long long* counters) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_cand) return;
   float2* out = P + i * n_ref;
@@ -69,27 +71,18 @@ __global__ void __launch_bounds__(kDedupThreads)
     for (int k = 0; k < n_ref; ++k) out[k] = make_float2(nan, nan);
     return;
   }
-  double r[3], v[3];
-  for (int c = 0; c < 3; ++c) {
-    r[c] = states[c * n + o];
-    v[c] = states[(c + 3) * n + o];
-  }
-  double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  double inv_r = 1.0 / rn;
-  const OrbitConst oc = orbit_const(ph, r, v, inv_r);
-  double t_prev = t0;
+  Track<DFS> w;
+  w.init(ph, states, n, o, t0, t_ref);
   bool failed = false;
   for (int k = 0; k < n_ref; ++k) {
     const ExpDev& e = ex[ref[k]];
     float2 p = make_float2(nan, nan);
     if (!failed) {
-      if (kepler_step(ph, oc, e.t - t_prev, r, v, rn, inv_r) < 0) {
+      dfloat rho[3];
+      if (!w.step(ph, e, rho)) {
         failed = true;
         atomicAdd(counters + 1, 1ull);
       } else {
-        t_prev = e.t;
-        dfloat rho[3];
-        apparent_rho_df(ph, r, v, inv_r, e, rho);
         float x, y;
         if (pixel_xy_df(e, rho, x, y)) p = make_float2(x, y);
       }
@@ -286,10 +279,10 @@ uint32_t dedup_table_size(int64_t n_cand) {
   return t;
 }
 
-cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64_t* cand, int64_t n_cand,
-                         const ExpDev* ex, const int32_t* ref_dev, int n_ref, Phys ph, float radius,
-                         void* scratch, unsigned long long* counters, int64_t* out, int* n_keep_dev,
-                         cudaStream_t st) {
+cudaError_t launch_dedup(const double* states, int64_t n, double t0, double t_ref, bool state_df,
+                         const int64_t* cand, int64_t n_cand, const ExpDev* ex, const int32_t* ref_dev,
+                         int n_ref, Phys ph, float radius, void* scratch, unsigned long long* counters,
+                         int64_t* out, int* n_keep_dev, cudaStream_t st) {
   if (n_cand == 0) return cudaMemsetAsync(n_keep_dev, 0, sizeof(int), st);
   const uint32_t table = dedup_table_size(n_cand);
   const int64_t nb = (n_cand + kScanBlock - 1) / kScanBlock;
@@ -313,8 +306,12 @@ cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64
   cudaError_t e = cudaMemsetAsync(first, 0, sizeof(int) * table, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(last, 0, sizeof(int) * table, st);
   if (e != cudaSuccess) return e;
-  k_track_ref<<<grid, kDedupThreads, 0, st>>>(states, n, t0, cand, n_cand, ex, ref_dev, n_ref, ph, P,
-                                              counters);
+  if (state_df)
+    k_track_ref<true><<<grid, kDedupThreads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, ref_dev, n_ref,
+                                                      ph, P, counters);
+  else
+    k_track_ref<false><<<grid, kDedupThreads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, ref_dev, n_ref,
+                                                       ph, P, counters);
   const float inv_cell2 = 0.5f / radius;       // cells of size 2r
   const uint32_t mask = table - 1;
   k_dedup_items<<<grid, kDedupThreads, 0, st>>>(P, (int)n_cand, n_ref, inv_cell2, mask, items_a);

@@ -44,11 +44,12 @@ static_assert(NPARAM == 52929, "parameter layout");
 // Positions along each candidate's track, compacted: entry k < cnt[i] of
 // candidate i is (ix << 16 | j, iy) for its k-th exposure j
 // (in epoch order) whose nearest pixel lies inside the image.  Before each
-// FP64 step, the FP32 off-chip test of the persistent stack
+// step, the FP32 off-chip test of the persistent stack
 // (certainly_off_chip, from the last computed state) removes the exposures
 // the track certainly misses: the state stays at its last epoch, and the
 // next computed step is longer (still exact).  In a sparse survey this
 // removes almost every step.
+template <bool DFS>
 __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ states, int64_t n,
                                                    double t0, double t_ref, const int64_t* __restrict__ cand,
                                                    int64_t n_cand, const ExpDev* __restrict__ ex,
@@ -62,37 +63,21 @@ __global__ void __launch_bounds__(128) k_stamp_pos(const double* __restrict__ st
     cnt[i] = 0;
     return;
   }
-  double r[3], v[3];
-  for (int c = 0; c < 3; ++c) {
-    r[c] = states[c * n + o];
-    v[c] = states[(c + 3) * n + o];
-  }
-  double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  double inv_r = 1.0 / rn;
-  const OrbitConst oc = orbit_const(ph, r, v, inv_r);
-  double t_prev = t0;
-  float rf[3], vf[3], tf = (float)(t0 - t_ref);
-  for (int c = 0; c < 3; ++c) {
-    rf[c] = d2f_trunc(r[c]);
-    vf[c] = d2f_trunc(v[c]);
-  }
+  Track<DFS> w;
+  w.init(ph, states, n, o, t0, t_ref);
+  float rf[3], vf[3], tf;
+  w.fp32(rf, vf, tf);
   int k = 0;
   for (int j = 0; j < n_exp; ++j) {
     const ExpDev& e = ex[j];
-    if (certainly_off_chip(ph, oc, rf, vf, tf, e)) continue;
-    if (kepler_step(ph, oc, e.t - t_prev, r, v, rn, inv_r) < 0) {
+    if (certainly_off_chip(ph, w.oc, rf, vf, tf, e)) continue;
+    dfloat rho[3];
+    if (!w.step(ph, e, rho)) {
       atomicAdd(counters + 1, 1ull);
       break;
     }
-    t_prev = e.t;
-    tf = e.tf;
-    for (int c = 0; c < 3; ++c) {
-      rf[c] = d2f_trunc(r[c]);
-      vf[c] = d2f_trunc(v[c]);
-    }
-    dfloat rho[3];
+    w.fp32(rf, vf, tf);
     int ix, iy;
-    apparent_rho_df(ph, r, v, inv_r, e, rho);
     if (pixel_of(e, rho, ix, iy)) out[k++] = make_int2((ix << 16) | j, iy);   // j < 2^16, ix < 2^15
   }
   cnt[i] = k;
@@ -456,17 +441,21 @@ cudaError_t launch_sigmoid(float* z, int64_t n, cudaStream_t st) {
 int cnn_param_count() { return NPARAM; }
 size_t cnn_smem_bytes() { return kCnnSmem; }
 
-cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref,
+cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref, bool state_df,
                                    const int64_t* cand, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                                    Phys ph, int2* pos, int* cnt, unsigned long long* counters,
                                    cudaStream_t st) {
   // one warp per block while the candidates do not fill every SM with four
-  // 128-thread blocks, so that they spread over all SMs (FP64-bound threads)
+  // 128-thread blocks, so that they spread over all SMs (latency-bound threads)
   const int threads = n_cand < 128 * 4 * 152 ? 32 : 128;
   const int64_t blocks = (n_cand + threads - 1) / threads;
   if (blocks == 0) return cudaSuccess;
-  k_stamp_pos<<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, n_exp, ph, pos,
-                                                    cnt, counters);
+  if (state_df)
+    k_stamp_pos<true><<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, n_exp, ph,
+                                                            pos, cnt, counters);
+  else
+    k_stamp_pos<false><<<(unsigned)blocks, threads, 0, st>>>(states, n, t0, t_ref, cand, n_cand, ex, n_exp, ph,
+                                                             pos, cnt, counters);
   return cudaGetLastError();
 }
 

@@ -191,69 +191,65 @@ constexpr double kInv24 = 1.0 / 24.0;
 
 struct OrbitConst {
   double alpha;        // 2/r - v^2/GM (reciprocal semi-major axis), conserved
-  double period;       // orbital period (bound orbits), else 0
-  double inv_period;
-  double half_period;  // steps longer than this are reduced modulo the period
-  double series_dt;    // steps shorter than this use the truncated f/g series
-  // FP32 copies for branch tests (compared on the FP32 pipe): the series
-  // bound shrunk by 1e-6 so that truncated |dt| never passes it wrongly
+  // FP32 bounds and thresholds (compared on the FP32 pipe): the series bounds
+  // shrunk so that truncated |dt| never passes them wrongly; half a period
+  // (bound orbits; steps beyond it are reduced modulo the period in FP64)
   float series_dt_f, tiny_dt_f, half_period_f, alpha_f;
   // bounds along the whole conic for the off-chip test (FP32): |d^3 r/dt^3| / 6,
   // GM / (2 q^2) >= |acceleration| / 2, and the perihelion speed v_q >= |v|
   float jerk6, half_acc, vq;
 };
 
-// (out of line: once per orbit and tile, its divisions and roots would
-// otherwise sit in the instruction stream of the walk)
-static __device__ __noinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
-                                                      const double v[3], double inv_r) {
+// Bound for the f/g series: along the whole conic |u| = GM/r^3 <= GM/q^3,
+// |p| = |r.v|/r^2 <= v_q/q and |w| = |v^2/r^2 - u| <= v_q^2/q^2 + GM/q^3,
+// with q the perihelion distance and v_q the speed there (vis-viva).  With
+// K = GM/q^3 + v_q^2/q^2 and dt^2 K <= 1e-7 the neglected terms of the
+// series stay at FP64 rounding (see fg_series_step).
+//
+// alpha and the semi-latus rectum p = |r x v|^2 / GM are FP64 (the cross
+// product cancels for nearly radial motion); the rest is FP32 and errs only
+// on the safe side: e from sqrt(1 - p alpha) with its radicand raised by
+// 1e-6 max(1, |p alpha|) (more than its FP32 rounding), q = p / (1 + e)
+// lowered by 1e-6, and with that q the vis-viva v_q^2 = GM (2/q - alpha),
+// K, |jerk| and |acceleration| are over-estimates, K and the bounds raised
+// by a further 1e-5 and the step thresholds lowered by 1e-5 for their own
+// FP32 rounding.  Near-circular orbits (radicand ~0) lose ~3e-4 of q this
+// way, about 1e-3 of K.
+__device__ __forceinline__ OrbitConst orbit_const(const Phys& ph, const double r[3],
+                                                  const double v[3], double inv_r) {
   OrbitConst oc;
-  double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
   oc.alpha = 2.0 * inv_r - v2 * ph.inv_gm;
-  if (oc.alpha > 0.0) {
-    double n = ph.sqrt_gm * oc.alpha * sqrt(oc.alpha);   // mean motion
-    oc.period = 6.283185307179586476925 / n;
-    oc.inv_period = n / 6.283185307179586476925;
-    oc.half_period = 0.5 * oc.period;
+  oc.alpha_f = (float)oc.alpha;
+  const double hx = r[1] * v[2] - r[2] * v[1], hy = r[2] * v[0] - r[0] * v[2],
+               hz = r[0] * v[1] - r[1] * v[0];
+  const float semi = (float)((hx * hx + hy * hy + hz * hz) * ph.inv_gm);
+  const float gm = ph.gm_f, sa = semi * oc.alpha_f;
+  const float ecc = sqrtf(fmaxf(0.0f, 1.0f - sa) + 1e-6f * fmaxf(1.0f, fabsf(sa)));
+  const float q = semi / (1.0f + ecc) * (1.0f - 1e-6f);
+  const float vq2 = gm * (2.0f / q - oc.alpha_f);
+  const float K = (gm / (q * q * q) + vq2 / (q * q)) * (1.0f + 1e-5f);
+  const bool ok = q > 0.0f && K > 0.0f && K < INFINITY;
+  oc.series_dt_f = ok ? sqrtf(1e-7f / K) * (1.0f - 1e-5f) : 0.0f;
+  oc.tiny_dt_f = ok ? sqrtf(3e-10f / K) * (1.0f - 1e-5f) : 0.0f;
+  oc.half_period_f = INFINITY;
+  if (oc.alpha_f > 0.0f)   // pi / n, n = sqrt(GM) alpha^1.5 (a threshold only)
+    oc.half_period_f = 3.14159265f / (sqrtf(gm) * oc.alpha_f * sqrtf(oc.alpha_f));
+  // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
+  // <= 4 GM v_q / q^3 anywhere on the conic (r >= q, |v| <= v_q).
+  if (ph.force_free) {
+    oc.jerk6 = 0.0f;
+    oc.half_acc = 0.0f;
+    oc.vq = sqrtf((float)v2) * (1.0f + 1e-5f);
+  } else if (ok && vq2 >= 0.0f) {
+    const float vq = sqrtf(vq2) * (1.0f + 1e-5f);
+    oc.jerk6 = 4.0f * gm * vq / (q * q * q) * (1.0f / 6.0f) * (1.0f + 1e-5f);
+    oc.half_acc = 0.5f * gm / (q * q) * (1.0f + 1e-5f);
+    oc.vq = vq;
   } else {
-    oc.period = 0.0;
-    oc.inv_period = 0.0;
-    oc.half_period = 1e300;
-  }
-  // Bound for the f/g series: along the whole conic |u| = GM/r^3 <= GM/q^3,
-  // |p| = |r.v|/r^2 <= v_q/q and |w| = |v^2/r^2 - u| <= v_q^2/q^2 + GM/q^3,
-  // with q the perihelion distance and v_q the speed there (vis-viva).  With
-  // K = GM/q^3 + v_q^2/q^2 and dt^2 K <= 1e-7 the neglected terms of the
-  // series stay at FP64 rounding (see fg_series_step).
-  {
-    const double hx = r[1] * v[2] - r[2] * v[1], hy = r[2] * v[0] - r[0] * v[2],
-                 hz = r[0] * v[1] - r[1] * v[0];
-    const double semi_latus = (hx * hx + hy * hy + hz * hz) * ph.inv_gm;
-    const double ecc = sqrt(fmax(0.0, 1.0 - semi_latus * oc.alpha));
-    const double q = semi_latus / (1.0 + ecc);
-    const double vq2 = ph.gm * (2.0 / q - oc.alpha);
-    const double K = ph.gm / (q * q * q) + vq2 / (q * q);
-    oc.series_dt = (q > 0.0 && K > 0.0 && K < 1e300) ? sqrt(1e-7 / K) : 0.0;
-    oc.series_dt_f = (float)(oc.series_dt * (1.0 - 1e-6));
-    oc.tiny_dt_f = (q > 0.0 && K > 0.0 && K < 1e300) ? (float)(sqrt(3e-10 / K) * (1.0 - 1e-6)) : 0.0f;
-    oc.half_period_f = oc.half_period < 1e30 ? (float)oc.half_period : INFINITY;
-    oc.alpha_f = (float)oc.alpha;
-    // d^3r/dt^3 = -GM (v / r^3 - 3 r (r.v) / r^5), so |d^3r/dt^3| <= 4 GM |v| / r^3
-    // <= 4 GM v_q / q^3 anywhere on the conic (r >= q, |v| <= v_q).
-    if (ph.force_free) {
-      oc.jerk6 = 0.0f;
-      oc.half_acc = 0.0f;
-      oc.vq = (float)sqrt(v2);
-    } else if (q > 0.0 && vq2 >= 0.0 && K < 1e300) {
-      const double vq = sqrt(vq2);
-      oc.jerk6 = (float)(4.0 * ph.gm * vq / (q * q * q) * kInv6);
-      oc.half_acc = (float)(0.5 * ph.gm / (q * q));
-      oc.vq = (float)vq;
-    } else {
-      oc.jerk6 = INFINITY;   // degenerate conic: never declared off-chip
-      oc.half_acc = INFINITY;
-      oc.vq = INFINITY;
-    }
+    oc.jerk6 = INFINITY;   // degenerate conic: never declared off-chip
+    oc.half_acc = INFINITY;
+    oc.vq = INFINITY;
   }
   return oc;
 }
@@ -406,7 +402,11 @@ __device__ __forceinline__ int kepler_step(const Phys& ph, const OrbitConst& oc,
     return 0;
   }
   // (reducing a step just under half a period changes nothing: rint gives 0 or +-1)
-  if (adtf > oc.half_period_f) dt = fma(-rint(dt * oc.inv_period), oc.period, dt);
+  if (adtf > oc.half_period_f) {   // bound orbit, step beyond half a period: reduce it
+    const double n = ph.sqrt_gm * oc.alpha * sqrt(oc.alpha);       // mean motion
+    const double period = 6.283185307179586476925 / n;
+    dt = fma(-rint(dt * (n * 0.15915494309189533577)), period, dt);
+  }
   const double alpha = oc.alpha;
   const double sig0 = (r[0] * v[0] + r[1] * v[1] + r[2] * v[2]) * ph.inv_sqrt_gm;
   const double a1 = fma(-alpha, rn, 1.0);            // 1 - alpha r0
@@ -786,6 +786,82 @@ __device__ __forceinline__ void apparent_rho_d(const Phys& ph, const double r[3]
   for (int i = 0; i < 3; ++i) rho[i] += -tau * v[i] + h * r[i] + k * (v[i] - 3.0 * p * r[i]);
 }
 
+// One orbit's walk through exposures in epoch order, for the kernels that
+// need its positions (candidate stage): Track<false> carries the FP64 state,
+// Track<true> the double-float one, as the stack's two forms do.  step()
+// moves the state to the exposure's epoch and gives the light-time corrected
+// topocentric vector (double-float); false on a Kepler failure.  fp32() is
+// the FP32 view of the state and its epoch - t_ref for the off-chip test.
+template <bool DFS>
+struct Track;
+
+template <>
+struct Track<false> {
+  OrbitConst oc;
+  double r[3], v[3], rn, inv_r, t;
+  float tf;
+  __device__ __forceinline__ void init(const Phys& ph, const double* __restrict__ states, int64_t n, int64_t o,
+                                       double t0, double t_ref) {
+    for (int c = 0; c < 3; ++c) {
+      r[c] = states[c * n + o];
+      v[c] = states[(c + 3) * n + o];
+    }
+    rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    inv_r = 1.0 / rn;
+    oc = orbit_const(ph, r, v, inv_r);
+    t = t0;
+    tf = (float)(t0 - t_ref);
+  }
+  __device__ __forceinline__ bool step(const Phys& ph, const ExpDev& e, dfloat rho[3]) {
+    if (kepler_step(ph, oc, e.t - t, r, v, rn, inv_r) < 0) return false;
+    t = e.t;
+    tf = e.tf;
+    apparent_rho_df(ph, r, v, inv_r, e, rho);
+    return true;
+  }
+  __device__ __forceinline__ void fp32(float rf[3], float vf[3], float& tfo) const {
+    for (int c = 0; c < 3; ++c) {
+      rf[c] = d2f_trunc(r[c]);
+      vf[c] = d2f_trunc(v[c]);
+    }
+    tfo = tf;
+  }
+};
+
+template <>
+struct Track<true> {
+  OrbitConst oc;
+  StateDF s;
+  dfloat tp;
+  __device__ __forceinline__ void init(const Phys& ph, const double* __restrict__ states, int64_t n, int64_t o,
+                                       double t0, double t_ref) {
+    double r[3], v[3];
+    for (int c = 0; c < 3; ++c) {
+      r[c] = states[c * n + o];
+      v[c] = states[(c + 3) * n + o];
+    }
+    const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    const double inv_r = 1.0 / rn;
+    oc = orbit_const(ph, r, v, inv_r);
+    s = state_df(r, v, rn, inv_r);
+    tp = split_df(t0 - t_ref);
+  }
+  __device__ __forceinline__ bool step(const Phys& ph, const ExpDev& e, dfloat rho[3]) {
+    const dfloat te = {e.tf, e.tf_l};
+    if (kepler_step_df(ph, oc, df_sub(te, tp), s) < 0) return false;
+    tp = te;
+    apparent_rho_dfs(ph, s.r, s.v, s.ir.h, e, rho);
+    return true;
+  }
+  __device__ __forceinline__ void fp32(float rf[3], float vf[3], float& tfo) const {
+    for (int c = 0; c < 3; ++c) {
+      rf[c] = s.r[c].h;
+      vf[c] = s.v[c].h;
+    }
+    tfo = tp.h;
+  }
+};
+
 // TAN projection through the precomputed per-exposure rows (Calabretta &
 // Greisen 2002, sec. 5.1.3, written with the tangent-plane basis vectors).
 // Gives the pixel coordinates shifted by one half, (x + 1/2, y + 1/2), so
@@ -1021,10 +1097,10 @@ size_t sort_hist_bytes(int64_t k);
 // duplicate suppression of ranked candidates (k_dedup.cu)
 uint32_t dedup_table_size(int64_t n_cand);
 size_t dedup_scratch_bytes(int64_t n_cand, int n_ref, uint32_t table);
-cudaError_t launch_dedup(const double* states, int64_t n, double t0, const int64_t* cand, int64_t n_cand,
-                         const ExpDev* ex, const int32_t* ref_dev, int n_ref, Phys ph, float radius,
-                         void* scratch, unsigned long long* counters, int64_t* out, int* n_keep_dev,
-                         cudaStream_t st);
+cudaError_t launch_dedup(const double* states, int64_t n, double t0, double t_ref, bool state_df,
+                         const int64_t* cand, int64_t n_cand, const ExpDev* ex, const int32_t* ref_dev,
+                         int n_ref, Phys ph, float radius, void* scratch, unsigned long long* counters,
+                         int64_t* out, int* n_keep_dev, cudaStream_t st);
 
 // vetting (stamps + CNN)
 int cnn_param_count();
@@ -1033,7 +1109,7 @@ int cnn_backward_blocks(int64_t n, int n_sms);
 // Compacted track positions of candidates: pos[i * n_exp + k], k < cnt[i],
 // = (ix << 16 | exposure, iy) of the k-th exposure (epoch order) whose
 // nearest pixel is inside the image (exposures < 2^16, widths <= 2^15).
-cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref,
+cudaError_t launch_stamp_positions(const double* states, int64_t n, double t0, double t_ref, bool state_df,
                                    const int64_t* cand, int64_t n_cand, const ExpDev* ex, int32_t n_exp,
                                    Phys ph, int2* pos, int* cnt, unsigned long long* counters,
                                    cudaStream_t st);
