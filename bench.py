@@ -65,8 +65,7 @@ FP64_MIX = {("mba", "chosen"): (0.760, 0.324, 0.041),
 # captured launch, same small cases as above) x computed samples over the
 # kernel's CUDA-event time, against that peak.
 ISSUE_PEAK_G = 152 * 4 * 2.07
-ISSUE_PER_SAMPLE = {("mba", "chosen"): 39.80, ("batched", "chosen"): 49.97,
-                    ("mba", "chosen_fp64_state"): 46.43}
+ISSUE_PER_SAMPLE = {("mba", "chosen"): 39.80, ("batched", "chosen"): 49.97}
 # DRAM bytes (read + write) of one stack launch on the small MBA case above
 # (200 exposures of 1024 x 1024, 512 orbits per family; BF16 planes 0.84 GB,
 # FP32 1.68 GB, both larger than L2), ncu dram__bytes_read.sum +
