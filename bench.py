@@ -51,8 +51,8 @@ FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 # samples; chosen 8.637e7 computed); batched: 128 families and 512 x 512
 # images (chosen 2.022e8 computed samples; its FP64-state figure, 2.037e8,
 # predates the block test).
-FP64_MIX = {("mba", "chosen"): (0.760, 0.324, 0.041),
-            ("batched", "chosen"): (6.589, 3.657, 0.760),
+FP64_MIX = {("mba", "chosen"): (0.119, 0.059, 0.012),
+            ("batched", "chosen"): (2.692, 1.458, 0.314),
             ("mba", "chosen_fp64_state"): (24.21, 13.56, 1.99),
             ("mba", "plain"): (23.27, 12.05, 1.99),
             ("mba", "plain_fp64"): (68.27, 43.06, 8.00),
@@ -65,7 +65,7 @@ FP64_MIX = {("mba", "chosen"): (0.760, 0.324, 0.041),
 # captured launch, same small cases as above) x computed samples over the
 # kernel's CUDA-event time, against that peak.
 ISSUE_PEAK_G = 152 * 4 * 2.07
-ISSUE_PER_SAMPLE = {("mba", "chosen"): 39.80, ("batched", "chosen"): 49.97}
+ISSUE_PER_SAMPLE = {("mba", "chosen"): 38.61, ("batched", "chosen"): 48.02}
 # DRAM bytes (read + write) of one stack launch on the small MBA case above
 # (200 exposures of 1024 x 1024, 512 orbits per family; BF16 planes 0.84 GB,
 # FP32 1.68 GB, both larger than L2), ncu dram__bytes_read.sum +
@@ -73,7 +73,7 @@ ISSUE_PER_SAMPLE = {("mba", "chosen"): 39.80, ("batched", "chosen"): 49.97}
 # the on-chip samples).  Family members read the same pixels, so traffic
 # grows more slowly than the orbit count: it is not scaled to the full
 # launch, whose own traffic stays null.
-TRAFFIC_SMALL_CASE = {("mba", "chosen"): (194741760, 343890136),
+TRAFFIC_SMALL_CASE = {("mba", "chosen"): (160923648, 343890136),
                       ("mba", "chosen_fp64_state"): (142069504, 343890136),
                       ("mba", "plain"): (177362176, 687780272),
                       ("mba", "plain_fp64"): (177615104, 687780272)}

@@ -263,7 +263,7 @@ ndt_status ndt_set_fp64_geometry(ndt_ctx *ctx, int32_t enabled);
    selects the FP64 state): stack_orbits (both forms) and predict_positions
    carry each orbit's position, velocity and 1/|r| as FP32 pairs (~48 bits)
    through the f and g series steps (to dt^2 K <= 1e-6, one order beyond the
-   FP64 series) and the universal-variable step where |alpha chi^2| <= 1e-2
+   FP64 series) and the universal-variable step where |alpha chi^2| <= 5e-2
    (paper sec. 3, two-body motion about the Sun); other steps convert to
    FP64, step and convert back.  On this GPU FP64 instructions retire at 1/64
    of the FP32 rate, and with an FP64 state they bound the stacking kernel.

@@ -50,9 +50,14 @@ NDT_HD float fma_rn(float a, float b, float c) {
   return std::fmaf(a, b, c);
 #endif
 }
+// 1/a to about an ulp (the hardware approximation on the device, one
+// instruction; subnormal inputs and results flush to zero): the quotient
+// and square-root corrections below need no more
 NDT_HD float rcp_approx(float a) {
 #ifdef __CUDA_ARCH__
-  return __frcp_rn(a);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
 #else
   return 1.0f / a;
 #endif
@@ -106,7 +111,7 @@ NDT_HD dfloat df_dot3(const dfloat a[3], const dfloat b[3]) {
   return fast_two_sum(s2.h, add_rn(low, add_rn(s1.l, s2.l)));
 }
 
-// n / d (d != 0); relative error ~2^-46
+// n / d (d != 0); relative error ~2^-45
 NDT_HD dfloat df_div(dfloat n, dfloat d) {
   const float r = rcp_approx(d.h);
   const float q1 = mul_rn(n.h, r);
@@ -116,9 +121,13 @@ NDT_HD dfloat df_div(dfloat n, dfloat d) {
   return fast_two_sum(q1, mul_rn(rem, r));
 }
 
+// sqrt(a) to about an ulp (the hardware approximation on the device): the
+// Newton correction of df_sqrt removes its error
 NDT_HD float sqrt_rn(float a) {
 #ifdef __CUDA_ARCH__
-  return __fsqrt_rn(a);
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
 #else
   return std::sqrt(a);
 #endif
@@ -136,7 +145,7 @@ NDT_HD dfloat df_sqrt(dfloat a) {
   const float s = sqrt_rn(a.h);
   const dfloat sq = two_prod(s, s);
   const float res = add_rn(sub_rn(sub_rn(a.h, sq.h), sq.l), a.l);
-  return fast_two_sum(s, mul_rn(res, 0.5f / s));
+  return fast_two_sum(s, mul_rn(res, 0.5f * rcp_approx(s)));
 }
 
 NDT_HD dfloat df_add(dfloat a, dfloat b) {

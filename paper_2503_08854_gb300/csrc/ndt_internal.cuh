@@ -614,21 +614,26 @@ static __device__ __noinline__ int kepler_step_df_long(const Phys& ph, const Orb
 }
 
 // The universal-variable step of kepler_step in double-float, for steps
-// beyond the series' range with |z| = |alpha chi^2| <= 1e-2 (a day for a
-// main-belt orbit, z ~ 2e-5; a few days for an NEO).  F, F' and the outputs
-// are double-float; the Stumpff functions are 1/2 - z/24 and 1/6 - z/120 in
-// double-float plus the z^2 and z^3 terms in FP32 (below 1.4e-7, rounded to
-// 1e-14; the neglected z^4 terms are below 3e-15), which keeps chi to
-// ~1e-16 and the position to the state's rounding.  The Laguerre-Conway
+// beyond the series' range with |z| = |alpha chi^2| <= 5e-2 (a day gives
+// z ~ 2e-5 for a main-belt orbit, two weeks ~7e-3).  F, F' and the outputs
+// are double-float; the Stumpff functions are 1/2 + z (-1/24 + z/720) and
+// 1/6 + z (-1/120 + z/5040) in double-float plus the z^3 to z^5 terms in
+// FP32 (below 3.1e-9, rounded to 2e-16; the neglected z^6 terms are below
+// 2e-19).  An error dC in C moves chi by ~sigma0 chi^2 dC / r0, so the
+// position needs dC below ~1e-16 alpha / z: met over the whole range.  The Laguerre-Conway
 // correction delta, F'' and the stopping test are FP32 as in kepler_step,
 // and the outputs are taken at chi - delta to first order.  Returns the
 // number of evaluations, or 0 with the state untouched when |z| leaves the
-// range or 4 evaluations do not converge: the caller then takes the FP64
-// step.
+// range (the guess is held to 3e-2) or 4 evaluations do not converge: the
+// caller then takes the FP64 step.
 constexpr float kInv6h = (float)(1.0 / 6.0), kInv6l = (float)(1.0 / 6.0 - (double)(float)(1.0 / 6.0));
 constexpr float kInv24h = (float)(1.0 / 24.0), kInv24l = (float)(1.0 / 24.0 - (double)(float)(1.0 / 24.0));
 constexpr float kInv120h = (float)(1.0 / 120.0),
                 kInv120l = (float)(1.0 / 120.0 - (double)(float)(1.0 / 120.0));
+constexpr float kInv720h = (float)(1.0 / 720.0),
+                kInv720l = (float)(1.0 / 720.0 - (double)(float)(1.0 / 720.0));
+constexpr float kInv5040h = (float)(1.0 / 5040.0),
+                kInv5040l = (float)(1.0 / 5040.0 - (double)(float)(1.0 / 5040.0));
 
 __device__ __forceinline__ int kepler_uv_df(const Phys& ph, const OrbitConst& oc, dfloat dt, StateDF& s) {
   const dfloat r0 = df_mul(df_dot3(s.r, s.r), s.ir);
@@ -640,18 +645,23 @@ __device__ __forceinline__ int kepler_uv_df(const Phys& ph, const OrbitConst& oc
   const float irf = s.ir.h, uf = sdt.h * irf, sif = sig0.h * irf;
   const float chif =
       uf * fmaf(uf, fmaf(-uf * (1.0f / 6.0f), fmaf(-3.0f * sif, sif, irf - oc.alpha_f), -0.5f * sif), 1.0f);
-  if (!(fabsf(oc.alpha_f) * chif * chif <= 5e-3f)) return 0;
+  if (!(fabsf(oc.alpha_f) * chif * chif <= 3e-2f)) return 0;
   dfloat chi = {chif, 0.0f};
 #pragma unroll 1
   for (int it = 1; it <= 4; ++it) {
     const dfloat chi2 = df_mul(chi, chi);
     const dfloat z = df_mul(al, chi2);
     const float zf = z.h;
-    if (!(fabsf(zf) <= 1e-2f)) return 0;
-    const float tc = zf * zf * fmaf(-zf, 1.0f / 40320.0f, 1.0f / 720.0f);
-    const float ts = zf * zf * fmaf(-zf, 1.0f / 362880.0f, 1.0f / 5040.0f);
-    const dfloat C = df_add_f(df_add_f(df_mul(z, dfloat{-kInv24h, -kInv24l}), tc), 0.5f);
-    const dfloat S = df_add(df_add_f(df_mul(z, dfloat{-kInv120h, -kInv120l}), ts), dfloat{kInv6h, kInv6l});
+    if (!(fabsf(zf) <= 5e-2f)) return 0;
+    // C = 1/2 + z (-1/24 + z/720) + z^3 (-1/40320 + z/3628800 - z^2/479001600),
+    // S = 1/6 + z (-1/120 + z/5040) + z^3 (-1/362880 + z/39916800 - z^2/6227020800)
+    const float z3 = zf * zf * zf;
+    const float tc = z3 * fmaf(zf, fmaf(-zf, 1.0f / 479001600.0f, 1.0f / 3628800.0f), -1.0f / 40320.0f);
+    const float ts = z3 * fmaf(zf, fmaf(-zf, 1.0f / 6227020800.0f, 1.0f / 39916800.0f), -1.0f / 362880.0f);
+    const dfloat cz = df_mul(z, df_add(dfloat{-kInv24h, -kInv24l}, df_mul(z, dfloat{kInv720h, kInv720l})));
+    const dfloat sz = df_mul(z, df_add(dfloat{-kInv120h, -kInv120l}, df_mul(z, dfloat{kInv5040h, kInv5040l})));
+    const dfloat C = df_add_f(df_add_f(cz, tc), 0.5f);
+    const dfloat S = df_add(df_add_f(sz, ts), dfloat{kInv6h, kInv6l});
     const dfloat chi2C = df_mul(chi2, C);
     const dfloat chi3S = df_mul(df_mul(chi2, chi), S);
     const dfloat chi1mzS = df_mul(chi, df_add_f(df_neg(df_mul(z, S)), 1.0f));   // chi (1 - z S)
@@ -691,10 +701,10 @@ __device__ __forceinline__ int kepler_uv_df(const Phys& ph, const OrbitConst& oc
 // kepler_step for the double-float state: the series steps in double-float
 // (fg_series_step_df up to dt^2 K <= 1e-6, i.e. sqrt(10) times the FP64
 // series bound), then the double-float universal-variable step where |z| <=
-// 1e-2, every other step through FP64.  Returns as kepler_step does.
+// 5e-2, every other step through FP64.  Returns as kepler_step does.
 __device__ __forceinline__ int kepler_step_df(const Phys& ph, const OrbitConst& oc, dfloat dt, StateDF& s) {
-  const float adtf = fabsf(dt.h);   // within 2^-24 of |dt|: inside the 1e-6 shrink of the bounds
-  // (3.1622775 < sqrt(10); its product's rounding stays inside the 1e-6 shrink)
+  const float adtf = fabsf(dt.h);   // within 2^-24 of |dt|: inside the 1e-5 shrink of the bounds
+  // (3.1622775 < sqrt(10); its product's rounding stays inside the 1e-5 shrink)
   if (!ph.force_free && adtf <= oc.series_dt_f * 3.1622775f) {
     if (adtf <= oc.tiny_dt_f)
       fg_tiny_step_df(ph, oc, dt, s);
@@ -740,7 +750,7 @@ __device__ __forceinline__ void apparent_rho_dfs(const Phys& ph, const dfloat R[
   const float dr = fmaf(rho[0].h, R[0].h, fmaf(rho[1].h, R[1].h, rho[2].h * R[2].h));
   const float pf = fmaf(R[0].h, V[0].h, fmaf(R[1].h, V[1].h, R[2].h * V[2].h)) * irf * irf;
   const float corr = fmaf(-dv, ph.inv_c2,
-                          0.5f * ph.inv_c3 * fmaf(dist.h, fmaf(-uf, dr, v2), dv * dv / dist.h));
+                          0.5f * ph.inv_c3 * fmaf(dist.h, fmaf(-uf, dr, v2), dv * dv * rcp_approx(dist.h)));
   const dfloat tau = df_add(df_mul(dist, {ph.inv_c, ph.inv_c_l}), {corr, 0.0f});
   const float hf = -0.5f * uf * tau.h * tau.h;                    // -(tau^2/2) u
   const float kf = uf * tau.h * tau.h * tau.h * (1.0f / 6.0f);    // (tau^3/6) u
