@@ -477,8 +477,8 @@ def vet_batch_rate(args, ctx, stream, sky, states, vet_params, device):
 
 def noise_rate(device, stream, imgs):
     """Iterative-MAD noise estimate of every image (ndt_noise_mad), timed
-    with CUDA events; its roofline is the HBM read rate (each selection pass
-    streams the image once: 6 passes per round)."""
+    with CUDA events; its roofline is the HBM read rate (each selection
+    pass streams the image once; the library counts the bytes)."""
     import torch
     from paper_2503_08854_gb300 import ndt
     ctx = ndt.create(device.index, stream)
@@ -492,11 +492,12 @@ def noise_rate(device, stream, imgs):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
+        read = float(ndt.get_stats(ctx)["noise_bytes_read"])
     finally:
         ndt.destroy(ctx)
-    read = float(np.sum(6 * rnd.astype(np.float64) * 4 * views[0].numel()))
     return {"images": len(views), "ms": ms, "rounds_max": int(rnd.max()), "rounds_mean": float(rnd.mean()),
-            "read_bytes": read, "read_gbps": read / (ms / 1e3) / 1e9}
+            "read_bytes": read, "passes_per_image": read / (4.0 * views[0].numel() * len(views)),
+            "read_gbps": read / (ms / 1e3) / 1e9}
 
 
 def bench_e2e(args, ctx, stream, sky, imgs, states, cand_dev, form, barrier, device):

@@ -102,6 +102,9 @@ typedef struct {
                                 time and projection the off-chip test
                                 removed (persistent form)                   */
   int64_t block_skipped;     /* of which the block cone test removed         */
+  int64_t noise_bytes_read;  /* image bytes the last noise estimate streamed
+                                (ndt_noise_mad, or load_exposures estimating
+                                variances)                                  */
 } ndt_stats;
 
 typedef struct ndt_ctx ndt_ctx;
@@ -343,7 +346,12 @@ ndt_status ndt_cnn_adam_step(ndt_ctx *ctx, float *params, const float *grad, flo
  * repeated until (m, sigma) repeats or max_rounds (1..100) rounds; outputs
  * median_out[i], sigma_out[i] and rounds_out[i] (any may be NULL; host or
  * device, caller-owned).  The result is exact: FP32 operations as written
- * and exact order statistics.  An image with no pixels gives NaN.
+ * and exact order statistics.  An image with no pixels gives NaN; an
+ * image of more than 2^32 - 1 pixels, a null image with pixels or
+ * max_rounds outside 1..100 gives NDT_EINVAL.  Device memory of the
+ * context: about 1 MB per image (the selection's key buffer) plus a staging
+ * copy of host images.  A selection usually streams the image once or
+ * twice (ndt_stats.noise_bytes_read counts the bytes).
  * load_exposures uses the same estimate (variance = sigma^2) for exposures
  * whose variance is <= 0 when no variance planes are given.  Synchronous.
  */

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <limits>
 #include <numeric>
@@ -80,7 +81,8 @@ struct ndt_ctx {
   // duplicate suppression
   DevBuf dedup_scratch, dedup_ref, dedup_out, count_dev;
   // noise estimate
-  DevBuf mad_imgs, mad_state, mad_hist, mad_stage;
+  DevBuf mad_imgs, mad_state, mad_hist, mad_stage, mad_cnt, mad_buf;
+  int64_t noise_bytes_read = 0;     // image bytes the last noise estimate streamed
   std::vector<float> noise_sigma;   // per exposure (table order): estimated sigma, or 0 if given
   // launch form
   int32_t mode = NDT_LAUNCH_PLAIN, orbit_tile = 64, exp_tile = 16, use_graph = 0;
@@ -253,13 +255,16 @@ float filter_sigma(const ndt_ctx* ctx, float psf_sigma) {
 
 void record(ndt_ctx* c, int i) { cudaEventRecord(c->ev[i], c->stream); }
 
-// Iterative-MAD noise estimate of device images (k_mad.cu); one round of six
-// selection passes per launch_mad_round, until every image reaches its fixed
-// point or max_rounds.  out[i] is the final state of image i.
+// Iterative-MAD noise estimate of device images (k_mad.cu): (pass, pick)
+// launches in groups of four until every image reaches its fixed point or
+// max_rounds; a selection takes one to five passes, so 10 per round bound
+// the loop.  out[i] is the final state of image i; the image bytes streamed
+// are added to the context's statistics.
 ndt_status mad_estimate(ndt_ctx* ctx, const std::vector<const float*>& dev_imgs,
                         const std::vector<int64_t>& n_pix, int max_rounds, std::vector<MadState>& out) {
   const int k = (int)dev_imgs.size();
-  out.assign(k, MadState{});
+  out.assign(k, mad_initial_state());
+  ctx->noise_bytes_read = 0;
   if (k == 0) return NDT_OK;
   std::vector<MadImage> h(k);
   int64_t max_n = 0;
@@ -267,18 +272,26 @@ ndt_status mad_estimate(ndt_ctx* ctx, const std::vector<const float*>& dev_imgs,
     h[i] = MadImage{dev_imgs[i], n_pix[i]};
     max_n = std::max(max_n, n_pix[i]);
   }
+  const uint32_t cap = (uint32_t)std::min<int64_t>(kMadCap, std::max<int64_t>(max_n, 1));
   NDT_CK(ctx->mad_imgs.ensure(sizeof(MadImage) * k), "noise image table");
   NDT_CK(ctx->mad_state.ensure(sizeof(MadState) * k), "noise state");
   NDT_CK(ctx->mad_hist.ensure(4 * mad_hist_words(k)), "noise histogram");
+  NDT_CK(ctx->mad_cnt.ensure(4 * (size_t)k), "noise counters");
+  NDT_CK(ctx->mad_buf.ensure(4 * (size_t)k * cap), "noise key buffer");
   NDT_CK(cudaMemcpyAsync(ctx->mad_imgs.p, h.data(), sizeof(MadImage) * k, cudaMemcpyHostToDevice, ctx->stream),
          "upload");
-  NDT_CK(cudaMemsetAsync(ctx->mad_state.p, 0, sizeof(MadState) * k, ctx->stream), "memset");
+  NDT_CK(cudaMemcpyAsync(ctx->mad_state.p, out.data(), sizeof(MadState) * k, cudaMemcpyHostToDevice,
+                         ctx->stream), "upload");
   NDT_CK(cudaMemsetAsync(ctx->mad_hist.p, 0, 4 * mad_hist_words(k), ctx->stream), "memset");
-  for (int r = 0; r < max_rounds; ++r) {
-    NDT_CK(launch_mad_round(ctx->mad_imgs.as<MadImage>(), ctx->mad_state.as<MadState>(),
-                            ctx->mad_hist.as<uint32_t>(), k, max_n, max_rounds, ctx->stream),
+  NDT_CK(cudaMemsetAsync(ctx->mad_cnt.p, 0, 4 * (size_t)k, ctx->stream), "memset");
+  constexpr int kGroup = 4;
+  const int max_pairs = 10 * max_rounds + kGroup;
+  for (int p = 0; p < max_pairs; p += kGroup) {
+    NDT_CK(launch_mad_passes(ctx->mad_imgs.as<MadImage>(), ctx->mad_state.as<MadState>(),
+                             ctx->mad_hist.as<uint32_t>(), ctx->mad_cnt.as<uint32_t>(),
+                             ctx->mad_buf.as<uint32_t>(), cap, k, max_n, max_rounds, kGroup, ctx->stream),
            "noise kernels");
-    ctx->launches += 12;
+    ctx->launches += 2 * kGroup;
     NDT_CK(cudaMemcpyAsync(out.data(), ctx->mad_state.p, sizeof(MadState) * k, cudaMemcpyDeviceToHost,
                            ctx->stream), "state D2H");
     NDT_CK(cudaStreamSynchronize(ctx->stream), "sync");
@@ -286,6 +299,7 @@ ndt_status mad_estimate(ndt_ctx* ctx, const std::vector<const float*>& dev_imgs,
     for (const MadState& st : out) all = all && st.done;
     if (all) break;
   }
+  for (int i = 0; i < k; ++i) ctx->noise_bytes_read += (int64_t)out[i].passes * 4 * n_pix[i];
   return NDT_OK;
 }
 
@@ -347,7 +361,7 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad,
                     &c->dedup_scratch, &c->dedup_ref, &c->dedup_out, &c->count_dev,
                     &c->trim_bits, &c->trim_nu, &c->trim_n, &c->mad_imgs, &c->mad_state,
-                    &c->mad_hist, &c->mad_stage};
+                    &c->mad_hist, &c->mad_stage, &c->mad_cnt, &c->mad_buf};
   for (DevBuf* b : bufs) b->release();
   delete c;   // (the DevBuf destructors free anything not listed above)
 }
@@ -1180,7 +1194,8 @@ ndt_status ndt_noise_mad(ndt_ctx* ctx, const float* const* images, const int64_t
   std::vector<int64_t> npx(n_pixels, n_pixels + n_images);
   int64_t host_total = 0;
   for (int i = 0; i < n_images; ++i) {
-    if (npx[i] < 0 || (npx[i] > 0 && !images[i])) return fail(ctx, NDT_EINVAL, "noise_mad: image %d", i);
+    if (npx[i] < 0 || npx[i] > (int64_t)UINT32_MAX || (npx[i] > 0 && !images[i]))
+      return fail(ctx, NDT_EINVAL, "noise_mad: image %d", i);
     if (npx[i] > 0 && !is_device_ptr(images[i])) host_total += npx[i];
   }
   if (host_total) NDT_CK(ctx->mad_stage.ensure(sizeof(float) * host_total), "noise staging");
@@ -1396,6 +1411,7 @@ ndt_status ndt_get_stats(ndt_ctx* ctx, ndt_stats* out) {
   out->kernel_launches = ctx->launches;
   out->offchip_skipped = (int64_t)cnt[3];
   out->block_skipped = (int64_t)cnt[4];
+  out->noise_bytes_read = ctx->noise_bytes_read;
   out->samples = ctx->samples;
   out->valid_samples = (int64_t)cnt[0];
   out->kepler_failures = (int64_t)cnt[1];

@@ -1132,17 +1132,32 @@ struct MadImage {
   int64_t n;
 };
 struct MadState {
-  int32_t done, round, rounds, pad_;
-  long long n_kept;
-  unsigned long long krem;   // rank still wanted inside the chosen digits
-  uint32_t prefix;           // digits chosen so far
+  int32_t done, round, rounds;
+  int32_t what;              // selection in progress: 0 median of S_i, 1 its MAD
+  int32_t phase;             // next pass: 1 histogram, 2 compaction of the band
+  int32_t level;             // histogram level of this selection (0: the window)
+  int32_t shift;             // histogram bins are 2^shift keys wide
+  int32_t passes;            // image passes so far
+  uint32_t lo;               // first key of the first inner bin
+  uint32_t blo, bhi;         // band: only keys in [blo, bhi] are counted or copied
+  uint32_t slo, shi;         // speculative copy range of a histogram pass (none if slo > shi)
+  uint32_t pad_;
+  long long n_kept;          // |S_i|
+  unsigned long long krem;   // rank wanted among the keys of the band
   float m_prev, thr_prev;    // S_i = { |x - m_prev| <= thr_prev } (round > 0)
   float m_cur;               // median of this round
   float m_last, sigma;       // the last completed round's (median, sigma)
+  float rho[2];              // keys per key unit near the last median / MAD
+  uint32_t kpred[2];         // key of the last median / MAD
 };
 constexpr int kNoiseMaxRounds = 10;
-cudaError_t launch_mad_round(const MadImage* imgs, MadState* st, uint32_t* hist, int n_images,
-                             int64_t max_pixels, int max_rounds, cudaStream_t stream);
+// keys a selection may copy out per image (the buffer holds cap per image)
+constexpr uint32_t kMadCap = 1u << 18;
+MadState mad_initial_state();
+// n_pairs (pass, pick) launches of the iterative-MAD selection (k_mad.cu)
+cudaError_t launch_mad_passes(const MadImage* imgs, MadState* st, uint32_t* hist, uint32_t* cnt, uint32_t* buf,
+                              uint32_t cap, int n_images, int64_t max_pixels, int max_rounds, int n_pairs,
+                              cudaStream_t stream);
 size_t mad_hist_words(int n_images);
 
 size_t trim_scratch_words(int64_t n_cand, int32_t n_exp);

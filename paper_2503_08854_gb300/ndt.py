@@ -40,7 +40,8 @@ class Stats(C.Structure):
                 ("last_stack_ms", C.c_float), ("last_planes_ms", C.c_float),
                 ("last_topk_ms", C.c_float), ("orbit_tile", C.c_int32), ("exp_tile", C.c_int32),
                 ("launch_mode", C.c_int32), ("plane_dtype", C.c_int32),
-                ("offchip_skipped", C.c_int64), ("block_skipped", C.c_int64)]
+                ("offchip_skipped", C.c_int64), ("block_skipped", C.c_int64),
+                ("noise_bytes_read", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -36,6 +36,11 @@ def _images():
     out.append(np.full(4096, 3.25, np.float32))                   # constant: sigma 0
     out.append(np.array([-0.0, 0.0, 1.0, -1.0, 2.0, 0.5], np.float32))
     out.append((np.random.default_rng(9).integers(-3, 4, 100_000)).astype(np.float32))  # many ties
+    # far from zero with infinities: in round 0 the median's bin holds more
+    # keys than the selection buffer and is histogrammed again
+    x = (np.random.default_rng(3).normal(size=1 << 20) + 100.0).astype(np.float32)
+    x[np.random.default_rng(4).choice(x.size, 2000, replace=False)] = np.inf
+    out.append(x)
     return out
 
 
