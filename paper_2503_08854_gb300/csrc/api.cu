@@ -213,10 +213,15 @@ void derive_projection(const ndt_exposure& m, double eps, ExpDev& e) {
     e.ay_f[i] = b.h;
     e.ay_l[i] = b.l;
   }
-  for (int i = 0; i < 2; ++i) {
-    const dfloat c = split_df(e.crpix_h[i]);
-    e.crh_h[i] = c.h;
-    e.crh_l[i] = c.l;
+  // rows with the reference pixel folded in (x + 1/2 = (rho . axc) / (rho . p0)),
+  // summed in long double before the split
+  for (int i = 0; i < 3; ++i) {
+    const dfloat a = split_df((double)((long double)e.ax[i] + (long double)e.crpix_h[0] * e.p0[i]));
+    const dfloat b = split_df((double)((long double)e.ay[i] + (long double)e.crpix_h[1] * e.p0[i]));
+    e.axc_f[i] = a.h;
+    e.axc_l[i] = a.l;
+    e.ayc_f[i] = b.h;
+    e.ayc_l[i] = b.l;
   }
   e.crpix_f[0] = (float)m.crpix[0];
   e.crpix_f[1] = (float)m.crpix[1];

@@ -169,6 +169,52 @@ NDT_HD dfloat df_mul_f(dfloat a, float b) {
   return fast_two_sum(p.h, fma_rn(a.l, b, p.l));
 }
 
+// Increments of a double-float by products: x + (a b + c), with the product
+// a.h b.h formed exactly, its cross terms and the FP32 term c gathered in the
+// low part, and one normalisation at the end (16 FP32 instructions, where a
+// product, a sum and a second sum take 29).  c is a correction below 2^-24 of
+// |x| + |a b| (it is rounded with the low part); the error is then ~2^-47
+// (|x| + |a b|).
+// The _small form needs |a b| <= |x|, which a vector component need not meet
+// even when the vector's increment is small (a component of x may vanish):
+// it serves updates of one quantity by a fraction of itself.  The others
+// hold for any magnitudes.
+NDT_HD dfloat df_add_prod_small(dfloat x, dfloat a, dfloat b, float c) {
+  const dfloat p = two_prod(a.h, b.h);
+  const float lo = fma_rn(a.h, b.l, fma_rn(a.l, b.h, add_rn(p.l, c)));
+  const dfloat s = fast_two_sum(x.h, p.h);
+  return fast_two_sum(s.h, add_rn(s.l, add_rn(x.l, lo)));
+}
+NDT_HD dfloat df_add_prod(dfloat x, dfloat a, dfloat b, float c) {
+  const dfloat p = two_prod(a.h, b.h);
+  const float lo = fma_rn(a.h, b.l, fma_rn(a.l, b.h, add_rn(p.l, c)));
+  const dfloat s = two_sum(x.h, p.h);
+  return fast_two_sum(s.h, add_rn(s.l, add_rn(x.l, lo)));
+}
+// x + (a u + b w)
+NDT_HD dfloat df_add_prod2(dfloat x, dfloat a, dfloat u, dfloat b, dfloat w) {
+  const dfloat p = two_prod(a.h, u.h);
+  const dfloat q = two_prod(b.h, w.h);
+  const dfloat t = two_sum(p.h, q.h);
+  const float lo =
+      fma_rn(a.h, u.l, fma_rn(a.l, u.h, fma_rn(b.h, w.l, fma_rn(b.l, w.h, add_rn(p.l, add_rn(q.l, t.l))))));
+  const dfloat s = two_sum(x.h, t.h);
+  return fast_two_sum(s.h, add_rn(s.l, add_rn(x.l, lo)));
+}
+// a b + c for an FP32 c with |c| <= |a b| / 2
+NDT_HD dfloat df_fma_small(dfloat a, dfloat b, float c) {
+  const dfloat p = two_prod(a.h, b.h);
+  const dfloat s = fast_two_sum(p.h, c);
+  return fast_two_sum(s.h, fma_rn(a.h, b.l, fma_rn(a.l, b.h, add_rn(p.l, s.l))));
+}
+// x (1 + f) for an FP32 f with |f| <= 1/2
+NDT_HD dfloat df_add_scaled_small(dfloat x, float f) {
+  const dfloat p = two_prod(x.h, f);
+  const float lo = fma_rn(x.l, f, p.l);
+  const dfloat s = fast_two_sum(x.h, p.h);
+  return fast_two_sum(s.h, add_rn(s.l, add_rn(x.l, lo)));
+}
+
 // a 2^k (s = 2^k): exact
 NDT_HD dfloat df_scale2(dfloat a, float s) { return {mul_rn(a.h, s), mul_rn(a.l, s)}; }
 

@@ -42,10 +42,10 @@ __device__ __forceinline__ bool pixel_xy_df(const ExpDev& e, const dfloat R[3], 
   const dfloat P[3] = {{e.p0_f[0], e.p0_l[0]}, {e.p0_f[1], e.p0_l[1]}, {e.p0_f[2], e.p0_l[2]}};
   const dfloat den = df_dot3(R, P);
   if (!(den.h > 1e-30f)) return false;
-  const dfloat AX[3] = {{e.ax_f[0], e.ax_l[0]}, {e.ax_f[1], e.ax_l[1]}, {e.ax_f[2], e.ax_l[2]}};
-  const dfloat AY[3] = {{e.ay_f[0], e.ay_l[0]}, {e.ay_f[1], e.ay_l[1]}, {e.ay_f[2], e.ay_l[2]}};
-  const dfloat xh = df_add({e.crh_h[0], e.crh_l[0]}, df_div(df_dot3(R, AX), den));
-  const dfloat yh = df_add({e.crh_h[1], e.crh_l[1]}, df_div(df_dot3(R, AY), den));
+  const dfloat AX[3] = {{e.axc_f[0], e.axc_l[0]}, {e.axc_f[1], e.axc_l[1]}, {e.axc_f[2], e.axc_l[2]}};
+  const dfloat AY[3] = {{e.ayc_f[0], e.ayc_l[0]}, {e.ayc_f[1], e.ayc_l[1]}, {e.ayc_f[2], e.ayc_l[2]}};
+  const dfloat xh = df_div(df_dot3(R, AX), den);
+  const dfloat yh = df_div(df_dot3(R, AY), den);
   // the rows give x + 1/2 and y + 1/2
   x = (xh.h - 0.5f) + xh.l;
   y = (yh.h - 0.5f) + yh.l;

@@ -25,7 +25,7 @@ constexpr int kMaxPsfRadius = 16;  // R = ceil(4 sigma) with sigma <= 4
 constexpr int kMaxKeplerIters = 40;
 
 // Per-exposure constants on the device, derived on the host from the
-// exposure table (152 bytes).
+// exposure table (328 bytes).
 struct ExpDev {
   double t;          // epoch (days)
   double obs[3];     // observer, heliocentric ecliptic (AU)
@@ -44,15 +44,18 @@ struct ExpDev {
   float obs_f[3], p0_f[3], ax_f[3], ay_f[3], crpix_f[2];
   float ppr;         // largest pixel stretch per radian at the tangent point (||CD^-1|| in px/rad)
   float cos_far;     // cos(largest off-axis angle of the chip + 0.01 rad), or -2 (never)
-  // low parts of p0, ax, ay (their high parts are p0_f, ax_f, ay_f) and
-  // crpix_h as a high/low pair: the double-float projection of the stack
-  float p0_l[3], ax_l[3], ay_l[3], crh_h[2], crh_l[2];
+  // low parts of p0, ax, ay (their high parts are p0_f, ax_f, ay_f)
+  float p0_l[3], ax_l[3], ay_l[3];
+  // the double-float projection of the stack: rows with the reference pixel
+  // folded in, x + 1/2 = (rho . axc) / (rho . p0) with axc = ax + crpix_h[0] p0
+  // (and ayc = ay + crpix_h[1] p0), as high/low pairs
+  float axc_f[3], axc_l[3], ayc_f[3], ayc_l[3];
   float obs_l[3];    // low parts of obs (high parts: obs_f), for the double-float light time
   float chip_sin;    // sin of the chip cone's radius
   float tf_l;        // epoch - t_ref - tf: the epoch as the double-float pair (tf, tf_l)
   int32_t pad_;
 };
-static_assert(sizeof(ExpDev) == 296 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
+static_assert(sizeof(ExpDev) == 328 && sizeof(ExpDev) % 8 == 0, "ExpDev layout");
 
 struct Phys {
   double gm;        // GM_sun (AU^3/day^2); <= 0: force-free motion
@@ -499,11 +502,6 @@ __device__ __forceinline__ StateDF state_df(const double r[3], const double v[3]
   return s;
 }
 
-// R + (a R + b V), a and b double-float coefficients of the two-body update
-__device__ __forceinline__ dfloat df_update(dfloat R, dfloat a, dfloat b, dfloat V) {
-  return df_add(R, df_add(df_mul(a, R), df_mul(b, V)));
-}
-
 // fg_series_step with the state, u, p, t^2 and the FP64 parts in double-float,
 // and one order more, so that it holds for dt^2 K <= 1e-6 (sqrt(10) times the
 // FP64 series' range: 0.1-0.2 day for main-belt orbits, the gaps between
@@ -548,18 +546,18 @@ __device__ __forceinline__ void fg_series_step_df(const Phys& ph, const OrbitCon
   const dfloat gdm1 = df_add_f(A, Lf);
   dfloat rr[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i) rr[i] = df_update(s.r[i], fm1, g, s.v[i]);
+  for (int i = 0; i < 3; ++i) rr[i] = df_add_prod2(s.r[i], fm1, s.r[i], g, s.v[i]);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) s.v[i] = df_update(s.v[i], gdm1, fdot, s.r[i]);
+  for (int i = 0; i < 3; ++i) s.v[i] = df_add_prod2(s.v[i], gdm1, s.v[i], fdot, s.r[i]);
 #pragma unroll
   for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
   // 1/|r|: y0 = (1/r)(1 - p t), e = 1 - x y0^2 (|e| = O(dt^2 K) <= 1e-6),
   // y = y0 (1 + e/2 + 3 e^2/8), remainder 5 e^3 / 16 < 1e-18
   const dfloat x = df_dot3(s.r, s.r);
-  const dfloat y0 = df_sub(s.ir, df_mul(s.ir, df_mul(p, t)));
+  const dfloat y0 = df_add_prod_small(s.ir, df_neg(s.ir), df_mul(p, t), 0.0f);   // |p t| <= 1e-3
   const dfloat e = df_add_f(df_neg(df_mul(x, df_mul(y0, y0))), 1.0f);
   const dfloat c = df_add_f(df_scale2(e, 0.5f), 0.375f * e.h * e.h);
-  s.ir = df_add(y0, df_mul(y0, c));
+  s.ir = df_add_prod_small(y0, y0, c, 0.0f);
   s.rn = x.h * s.ir.h;
 }
 
@@ -581,19 +579,19 @@ __device__ __forceinline__ void fg_tiny_step_df(const Phys& ph, const OrbitConst
   const float gdm1f = fmaf(upf, t3f, Af);
   const dfloat g = df_add_f(t, gm1f);
   const dfloat fdot = df_add_f(df_neg(df_mul(u, t)), kf);
+  // (f - 1) r and (gdot - 1) v are below 1e-9 of the state: FP32 products
+  // (rounding below 1e-16 of it) in the low part of the double-float update
   dfloat rr[3];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    rr[i] = df_add(s.r[i], df_add(df_mul_f(s.r[i], fm1f), df_mul(g, s.v[i])));
+  for (int i = 0; i < 3; ++i) rr[i] = df_add_prod(s.r[i], g, s.v[i], fm1f * s.r[i].h);
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-    s.v[i] = df_add(s.v[i], df_add(df_mul_f(s.v[i], gdm1f), df_mul(fdot, s.r[i])));
+  for (int i = 0; i < 3; ++i) s.v[i] = df_add_prod(s.v[i], fdot, s.r[i], gdm1f * s.v[i].h);
 #pragma unroll
   for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
   const dfloat x = df_dot3(s.r, s.r);
-  const dfloat y0 = df_add(s.ir, df_mul_f(s.ir, -pf * tf));
+  const dfloat y0 = df_add_scaled_small(s.ir, -pf * tf);
   const dfloat e = df_add_f(df_neg(df_mul(x, df_mul(y0, y0))), 1.0f);
-  s.ir = df_add(y0, df_mul(y0, df_scale2(e, 0.5f)));
+  s.ir = df_add_scaled_small(y0, 0.5f * e.h);   // |e| <= ~1e-9: its low half is below 2^-53 of 1
   s.rn = x.h * s.ir.h;
 }
 
@@ -684,9 +682,9 @@ __device__ __forceinline__ int kepler_uv_df(const Phys& ph, const OrbitConst& oc
       const dfloat gdm1 = df_neg(df_mul(chi2C_c, inv_rc));                           // gdot - 1
       dfloat rr[3];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) rr[i] = df_update(s.r[i], fm1, g, s.v[i]);
+      for (int i = 0; i < 3; ++i) rr[i] = df_add_prod2(s.r[i], fm1, s.r[i], g, s.v[i]);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) s.v[i] = df_update(s.v[i], gdm1, fdot, s.r[i]);
+      for (int i = 0; i < 3; ++i) s.v[i] = df_add_prod2(s.v[i], gdm1, s.v[i], fdot, s.r[i]);
 #pragma unroll
       for (int i = 0; i < 3; ++i) s.r[i] = rr[i];
       s.ir = inv_rc;
@@ -751,14 +749,14 @@ __device__ __forceinline__ void apparent_rho_dfs(const Phys& ph, const dfloat R[
   const float pf = fmaf(R[0].h, V[0].h, fmaf(R[1].h, V[1].h, R[2].h * V[2].h)) * irf * irf;
   const float corr = fmaf(-dv, ph.inv_c2,
                           0.5f * ph.inv_c3 * fmaf(dist.h, fmaf(-uf, dr, v2), dv * dv * rcp_approx(dist.h)));
-  const dfloat tau = df_add(df_mul(dist, {ph.inv_c, ph.inv_c_l}), {corr, 0.0f});
+  const dfloat tau = df_fma_small(dist, {ph.inv_c, ph.inv_c_l}, corr);   // |corr| ~ 1e-4 |d|/c
   const float hf = -0.5f * uf * tau.h * tau.h;                    // -(tau^2/2) u
   const float kf = uf * tau.h * tau.h * tau.h * (1.0f / 6.0f);    // (tau^3/6) u
+  const dfloat ntau = df_neg(tau);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    const dfloat tv = df_mul(tau, V[i]);
     const float small = fmaf(hf, R[i].h, kf * fmaf(-3.0f * pf, R[i].h, V[i].h));
-    rho[i] = df_add(df_add(rho[i], {-tv.h, -tv.l}), {small, 0.0f});
+    rho[i] = df_add_prod(rho[i], ntau, V[i], small);
   }
 }
 
@@ -891,18 +889,18 @@ __device__ __forceinline__ bool project_h(const ExpDev& e, const double rho[3], 
 
 // Nearest pixel of a topocentric vector (double-float, from apparent_rho_df)
 // through the TAN projection in double-float arithmetic (~48-bit dot
-// products and quotient): the same x + 1/2 and
-// y + 1/2 as project_h to ~2e-8 px at 0.2 arcsec pixels (host check against
-// long double), with no FP64 instruction.  False when cos c <= 0 or outside
-// the image.
+// products and quotient, the reference pixel folded into the rows): the
+// same x + 1/2 and y + 1/2 as project_h to ~2e-8 px at 0.2 arcsec pixels
+// (host check against long double), with no FP64 instruction.  False when
+// cos c <= 0 or outside the image.
 __device__ __forceinline__ bool pixel_of(const ExpDev& e, const dfloat R[3], int& ix, int& iy) {
   const dfloat P[3] = {{e.p0_f[0], e.p0_l[0]}, {e.p0_f[1], e.p0_l[1]}, {e.p0_f[2], e.p0_l[2]}};
   const dfloat den = df_dot3(R, P);
   if (!(den.h > 1e-30f)) return false;
-  const dfloat AX[3] = {{e.ax_f[0], e.ax_l[0]}, {e.ax_f[1], e.ax_l[1]}, {e.ax_f[2], e.ax_l[2]}};
-  const dfloat AY[3] = {{e.ay_f[0], e.ay_l[0]}, {e.ay_f[1], e.ay_l[1]}, {e.ay_f[2], e.ay_l[2]}};
-  const dfloat xh = df_add({e.crh_h[0], e.crh_l[0]}, df_div(df_dot3(R, AX), den));
-  const dfloat yh = df_add({e.crh_h[1], e.crh_l[1]}, df_div(df_dot3(R, AY), den));
+  const dfloat AX[3] = {{e.axc_f[0], e.axc_l[0]}, {e.axc_f[1], e.axc_l[1]}, {e.axc_f[2], e.axc_l[2]}};
+  const dfloat AY[3] = {{e.ayc_f[0], e.ayc_l[0]}, {e.ayc_f[1], e.ayc_l[1]}, {e.ayc_f[2], e.ayc_l[2]}};
+  const dfloat xh = df_div(df_dot3(R, AX), den);
+  const dfloat yh = df_div(df_dot3(R, AY), den);
   ix = df_floor(xh);
   iy = df_floor(yh);
   return (unsigned)ix < (unsigned)e.W && (unsigned)iy < (unsigned)e.H;

@@ -55,7 +55,8 @@ int main() {
   // about six roundings of order 2^-48 of the terms: 2^-45.4; bound with a factor 2
   if (worst_dot > std::ldexp(1.0, -44)) ++bad;
   std::printf("dot: worst error / sum|a b| %.3g (bound 2^-44 = %.3g)\n", worst_dot, std::ldexp(1.0, -44));
-  // 3. TAN projection: x + 1/2 = crpix_h + (rho . ax) / (rho . p0), as the kernel forms it
+  // 3. TAN projection: x + 1/2 = crpix_h + (rho . ax) / (rho . p0), formed as
+  //    the kernel does, (rho . (ax + crpix_h p0)) / (rho . p0)
   double worst_px = 0.0;
   const double ppr = 1.0 / (0.2 / 3600.0 * M_PI / 180.0);   // px per radian at 0.2 arcsec
   for (int i = 0; i < 1000000; ++i) {
@@ -78,16 +79,17 @@ int main() {
     const double ox = 0.026 * U(rng), oy = 0.026 * U(rng);
     double rho[3];
     for (int k = 0; k < 3; ++k) rho[k] = dist * (p0[k] + ox * e1[k] + oy * e2[k]);
+    // the kernel's rows carry the reference pixel: axc = ax + crh[0] p0
     dfloat R[3], P[3], AX[3], AY[3];
     for (int k = 0; k < 3; ++k) {
       R[k] = ndt::split_df(rho[k]);
       P[k] = ndt::split_df(p0[k]);
-      AX[k] = ndt::split_df(ax[k]);
-      AY[k] = ndt::split_df(ay[k]);
+      AX[k] = ndt::split_df((double)((LD)ax[k] + (LD)crh[0] * (LD)p0[k]));
+      AY[k] = ndt::split_df((double)((LD)ay[k] + (LD)crh[1] * (LD)p0[k]));
     }
     const dfloat den = ndt::df_dot3(R, P);
-    const dfloat xh = ndt::df_add(ndt::split_df(crh[0]), ndt::df_div(ndt::df_dot3(R, AX), den));
-    const dfloat yh = ndt::df_add(ndt::split_df(crh[1]), ndt::df_div(ndt::df_dot3(R, AY), den));
+    const dfloat xh = ndt::df_div(ndt::df_dot3(R, AX), den);
+    const dfloat yh = ndt::df_div(ndt::df_dot3(R, AY), den);
     LD D = 0, NX = 0, NY = 0;
     for (int k = 0; k < 3; ++k) {
       D += (LD)rho[k] * (LD)p0[k];
@@ -121,6 +123,52 @@ int main() {
         return 1;
       }
     }
+  }
+  // 5. increments by products (the two-body and light-time updates):
+  //    x + (a b + c), x + (a u + b w), x (1 + f), against long double, with
+  //    increments from 1 down to 1e-12 of x (the _small forms) and of any
+  //    size (the general ones); error relative to |x| + |increments|
+  double worst_inc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < 1000000; ++i) {
+    const double xv = U(rng) * std::ldexp(1.0, (int)(rng() % 12) - 6);
+    const double sm = std::ldexp(1.0, -(int)(rng() % 40));           // |increment| / |x| scale
+    const double big = std::ldexp(1.0, (int)(rng() % 40) - 20);      // any ratio
+    const double av = U(rng) * sm, bv = xv * U(rng), cv = xv * sm * 1e-8 * U(rng);
+    const double a2 = U(rng) * big, u2 = xv * U(rng), b2 = U(rng) * big, w2 = U(rng);
+    const dfloat X = ndt::split_df(xv), A = ndt::split_df(av), B = ndt::split_df(bv);
+    const dfloat A2 = ndt::split_df(a2), U2 = ndt::split_df(u2), B2 = ndt::split_df(b2), W2 = ndt::split_df(w2);
+    const float c = (float)cv, f = (float)(0.5 * U(rng) * sm);
+    const LD x = val(X), a = val(A), b = val(B);
+    // |a b| <= |x| here: the _small form applies
+    LD want = x + (a * b + (LD)c);
+    LD mag = std::fabs(x) + std::fabs(a * b) + std::fabs((LD)c);
+    worst_inc[0] = std::fmax(worst_inc[0], (double)(std::fabs(val(ndt::df_add_prod_small(X, A, B, c)) - want) / mag));
+    worst_inc[1] = std::fmax(worst_inc[1], (double)(std::fabs(val(ndt::df_add_prod(X, A, B, c)) - want) / mag));
+    // general magnitudes
+    want = x + (val(A2) * val(U2) + val(B2) * val(W2));
+    mag = std::fabs(x) + std::fabs(val(A2) * val(U2)) + std::fabs(val(B2) * val(W2));
+    worst_inc[2] = std::fmax(worst_inc[2], (double)(std::fabs(val(ndt::df_add_prod2(X, A2, U2, B2, W2)) - want) / mag));
+    want = x * (1.0L + (LD)f);
+    worst_inc[3] = std::fmax(worst_inc[3], (double)(std::fabs(val(ndt::df_add_scaled_small(X, f)) - want) / std::fabs(x)));
+  }
+  // a b + c with |c| <= |a b| / 2 (the light time |d| / c + corr)
+  double worst_fma = 0.0;
+  for (int i = 0; i < 1000000; ++i) {
+    const dfloat A = ndt::split_df(U(rng) * std::ldexp(1.0, (int)(rng() % 20) - 10));
+    const dfloat B = ndt::split_df(U(rng) * std::ldexp(1.0, (int)(rng() % 20) - 10));
+    const LD ab = val(A) * val(B);
+    const float c = (float)(0.5 * (double)ab * U(rng) * std::ldexp(1.0, -(int)(rng() % 30)));
+    const LD want = ab + (LD)c;
+    worst_fma = std::fmax(worst_fma, (double)(std::fabs(val(ndt::df_fma_small(A, B, c)) - want) / std::fabs(ab)));
+  }
+  if (!(worst_fma <= std::ldexp(1.0, -45))) ++bad;
+  std::printf("a b + c: worst error / |a b| %.3g (bound 2^-45 = %.3g)\n", worst_fma, std::ldexp(1.0, -45));
+  const char* inc_names[4] = {"x + (a b + c), small", "x + (a b + c)", "x + (a u + b w)", "x (1 + f)"};
+  for (int k = 0; k < 4; ++k) {
+    // a handful of roundings of order 2^-48 of the largest term
+    if (!(worst_inc[k] <= std::ldexp(1.0, -45))) ++bad;
+    std::printf("%s: worst error / magnitude %.3g (bound 2^-45 = %.3g)\n", inc_names[k], worst_inc[k],
+                std::ldexp(1.0, -45));
   }
   std::printf("%s\n", bad ? "FAILED" : "ok");
   return bad ? 1 : 0;
