@@ -109,8 +109,9 @@ def parse():
     p.add_argument("--no-sparse", action="store_true",
                    help="skip the sparse-regime sub-record (MBA runs only)")
     p.add_argument("--vet-skies", type=int, default=12, help="vetting skies used for training")
-    p.add_argument("--vet-survey-stamps", type=int, default=200_000,
-                   help="MBA-like survey stamps in the vetting network's training set")
+    p.add_argument("--vet-train-stamps", type=int, default=200_000,
+                   help="stamps in the vetting network's training set (vetting skies, then MBA-like "
+                        "survey skies until the count is reached)")
     p.add_argument("--vet-batch", type=int, default=1 << 20,
                    help="candidates of the separately timed vetting pass (0: skip)")
     a = p.parse_args()
@@ -306,15 +307,15 @@ def run_steps(ctx, stream, sky, imgs, states, n_steps, plane, cand):
     return step_ms, stack_ms, cand_ms
 
 
-def train_vetter(device, seed=5, n_train_sky=12, n_test_sky=3, survey_stamps=200_000, max_survey_skies=16):
+def train_vetter(device, seed=5, n_train_sky=12, n_test_sky=3, train_stamps=200_000, max_survey_skies=24):
     """Untimed setup: synthesise vetting stamps with the library and train the
     CNN with the library's forward/backward/Adam kernels.  Two sources:
     vetting skies (injected asteroids vs random orbits, single-exposure
     artefacts and noise peaks, 10 exposures of 1024^2) and MBA-like survey
     skies (the MBA workload's cadence, chips, PSF and noise; positives are
     orbits tracking an injected asteroid within MATCH_PX, negatives orbits
-    that share only part of its path, and noise peaks) until the set holds
-    ``survey_stamps`` of the latter.  The false-positive rate at 90 % recall
+    that share only part of its path, and noise peaks) until the training
+    set holds ``train_stamps`` stamps in all.  The false-positive rate at 90 % recall
     is measured on held-out vetting skies here and on the MBA survey's own
     candidate list in the benchmark."""
     import torch
@@ -326,8 +327,8 @@ def train_vetter(device, seed=5, n_train_sky=12, n_test_sky=3, survey_stamps=200
         xs, ys = [], []
         x, y, kind, _ = vetting.make_set(ctx, seed, device, n_sky=n_train_sky)
         xs.append(x); ys.append(y)
-        n_survey, skies = 0, 0
-        while n_survey < survey_stamps and skies < max_survey_skies:
+        n_vet, n_survey, skies = int(x.shape[0]), 0, 0
+        while n_vet + n_survey < train_stamps and skies < max_survey_skies:
             x, y, _, _ = vetting.make_survey_set(ctx, seed * 100 + skies, device)
             xs.append(x); ys.append(y)
             n_survey += x.shape[0]
@@ -875,7 +876,7 @@ def main():
     if "chosen" in args.forms.split(",") and not args.no_vet:
         vet_params, vet_info = train_vetter(device, n_train_sky=args.vet_skies,
                                             n_test_sky=max(1, args.vet_skies // 4),
-                                            survey_stamps=args.vet_survey_stamps)
+                                            train_stamps=args.vet_train_stamps)
     sky, stream, imgs, states = make_workload(args, rank, device)
     forms = {"plain": Form("plain", "f32", "plain", False),
              "plain_fp64": Form("plain_fp64", "f32", "plain", False, geom64=True),

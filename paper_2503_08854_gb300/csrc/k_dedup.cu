@@ -151,13 +151,17 @@ __global__ void __launch_bounds__(kDedupThreads)
 }
 
 // keep[i] = 0 when a candidate of smaller rank (index) lies within r of i at
-// every reference exposure (both positions defined), else 1.
+// every reference exposure (both positions defined), else 1.  Thread q takes
+// the candidate at position q of the sorted items, so that the threads of a
+// bucket's run read the same bucket bounds, run entries and leading
+// neighbours (most candidates are duplicates of their bucket's first entry).
 __global__ void __launch_bounds__(kDedupThreads)
     k_dedup_mark(const float2* __restrict__ P, int n_cand, int n_ref, float inv_cell2, float r2,
                  const unsigned long long* __restrict__ items, const int* __restrict__ first,
                  const int* __restrict__ last, uint32_t mask, uint8_t* __restrict__ keep) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_cand) return;
+  const int q0 = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q0 >= n_cand) return;
+  const int i = (int)(unsigned)items[q0];
   const float2* pi = P + (int64_t)i * n_ref;
   GridKey g;
   bool dup = false;

@@ -256,37 +256,50 @@ __global__ void __launch_bounds__(kThreads) k_rs_hist(const unsigned long long* 
 }
 
 // Exclusive scan of the bin-major block histograms by one block of 1024
-// threads: warp shuffles inside each chunk of 1024, a carry across chunks.
+// threads: each warp owns one contiguous segment, read 32 consecutive counts
+// at a time (coalesced); the warp totals are scanned once, then each warp
+// rewrites its segment with running offsets, loading eight rounds ahead.
 __global__ void __launch_bounds__(1024) k_rs_scan(unsigned int* hist, int64_t total) {
+  constexpr unsigned kFull = 0xffffffffu;
+  constexpr int kAhead = 8;
   __shared__ unsigned int warp_sum[32];
-  __shared__ unsigned int carry;
-  if (threadIdx.x == 0) carry = 0u;
-  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t base = 0; base < total; base += 1024) {
-    const int64_t i = base + threadIdx.x;
-    const unsigned int v = i < total ? hist[i] : 0u;
-    unsigned int x = v;
+  const int64_t seg = (total + 1023) / 1024 * 32;        // a multiple of 32 per warp
+  const int64_t s0 = (int64_t)warp * seg, s1 = s0 + seg < total ? s0 + seg : total;
+  unsigned int mine = 0u;
+  for (int64_t i = s0 + lane; i < s1; i += 32) mine += hist[i];
+  mine = __reduce_add_sync(kFull, mine);
+  if (lane == 0) warp_sum[warp] = mine;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned int w0 = warp_sum[lane];
+    unsigned int w = w0;
     for (int o = 1; o < 32; o <<= 1) {
-      const unsigned int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const unsigned int y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
     }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned int w = warp_sum[lane];
+    warp_sum[lane] = w - w0;                            // exclusive
+  }
+  __syncthreads();
+  unsigned int carry = warp_sum[warp];
+  for (int64_t base = s0; base < s1; base += 32 * kAhead) {
+    unsigned int v[kAhead];
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      const int64_t i = base + u * 32 + lane;
+      v[u] = i < s1 ? hist[i] : 0u;
+    }
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      unsigned int x = v[u];
       for (int o = 1; o < 32; o <<= 1) {
-        const unsigned int y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
+        const unsigned int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
       }
-      warp_sum[lane] = w;
+      const int64_t i = base + u * 32 + lane;
+      if (i < s1) hist[i] = carry + x - v[u];
+      carry += __shfl_sync(kFull, x, 31);
     }
-    __syncthreads();
-    const unsigned int incl = x + (warp > 0 ? warp_sum[warp - 1] : 0u) + carry;
-    if (i < total) hist[i] = incl - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = incl;
-    __syncthreads();
   }
 }
 
