@@ -95,6 +95,33 @@ def test_planes_both_kernel_forms_match_oracle(gpu, plane, wide_psf):
         assert np.all(np.abs(phi - rf) <= tol_phi), (j, np.abs(phi - rf).max())
 
 
+@pytest.mark.parametrize("plane", ["f32", "bf16"])
+def test_planes_tma_form_many_strips(gpu, plane):
+    """The TMA form over 1,156 strips of 20 exposures at once (more CTAs than
+    the GPU holds), with different PSF widths, image sizes (ragged strips
+    and tiles) and variances per exposure: every plane matches the
+    oracle's."""
+    rng = np.random.default_rng(11)
+    sky = _ragged_sky(n_exp=20)
+    ex = sky.ex.subset(range(20))
+    ex.width = np.array([1024, 260, 768, 128, 1028] * 4, np.int32)
+    ex.height = np.array([512, 200, 420, 330, 140] * 4, np.int32)
+    ex.sigma = rng.uniform(1.2, 2.0, 20)
+    ex.var = rng.uniform(0.5, 2.0, 20)
+    imgs = [rng.normal(size=(ex.height[j], ex.width[j])).astype(np.float32) for j in range(20)]
+    d = [torch.from_numpy(im).to(gpu.dev) for im in imgs]
+    torch.cuda.synchronize()
+    ndt.load_exposures(gpu.ctx, ex, d, plane_dtype=plane)
+    rel = {"f32": 0.0, "bf16": 2.0 ** -8}[plane]
+    for j in range(20):
+        psi, phi = gpu.planes(j, ex.height[j], ex.width[j])
+        rp, rf = O.planes(imgs[j], ex.sigma[j], ex.var[j])
+        tol_psi = rel * np.abs(rp) + 1e-5 * np.abs(rp) + 2e-6 * np.abs(rp).max()
+        tol_phi = rel * np.abs(rf) + 1e-5 * np.abs(rf) + 1e-7 * rf.max()
+        assert np.all(np.abs(psi - rp) <= tol_psi), (j, np.abs(psi - rp).max())
+        assert np.all(np.abs(phi - rf) <= tol_phi), (j, np.abs(phi - rf).max())
+
+
 @pytest.mark.parametrize("plane", ["bf16", "f16"])
 def test_reduced_precision_planes_error_bound(gpu, plane):
     """RNE of value/scale: |error| <= half an ulp of the stored format (2^-9
