@@ -450,6 +450,16 @@ def bench_form(args, form, sky, stream, imgs, states, device, barrier, vet_param
         ndt.destroy(ctx)
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json beside
+    this file), else the 6.8 TB/s fallback of an earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def vet_batch_rate(args, ctx, stream, sky, states, vet_params, device):
     """Vetting throughput at the learned-vetting workload's scale: the top
     ``--vet-batch`` candidates of the stacked batch (ranked once, untimed)
@@ -472,8 +482,31 @@ def vet_batch_rate(args, ctx, stream, sky, states, vet_params, device):
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     t = statistics.mean(ms)
+    # the stamps alone (track positions + gathers), and their gather bytes:
+    # 441 plane pairs (4 B each, BF16) per in-bounds exposure of a candidate
+    stamps = torch.empty((m, 2, 21, 21), dtype=torch.int16, device=device)
+    ndt.stamps(ctx, states, sky.t0, n, idx, stamps_bf16=stamps)                # warm-up
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ndt.stamps(ctx, states, sky.t0, n, idx, stamps_bf16=stamps)
+    e1.record(stream)
+    e1.synchronize()
+    t_st = e0.elapsed_time(e1)
+    del stamps
+    nobs = torch.empty(n, dtype=torch.int32, device=device)
+    ndt.stack_orbits(ctx, states, sky.t0, n, families=sky.fam_dev, nobs=nobs)
+    ndt.synchronize(ctx)                       # nobs is read on torch's stream
+    pairs = int(nobs[idx].to(torch.int64).sum().item())
+    gather = pairs * 441 * 4
+    peak = hbm_peak_gbs()
     return {"candidates": m, "ms": t, "vetted_candidates_per_s": m / (t / 1e3),
-            "exposures": int(sky.ex.n)}
+            "exposures": int(sky.ex.n),
+            "stamps": {"ms": t_st, "in_bounds_pairs": pairs, "gather_bytes": gather,
+                       "gather_gbs": gather / (t_st / 1e3) / 1e9, "hbm_peak_gbs": peak,
+                       "frac_of_hbm": gather / (t_st / 1e3) / 1e9 / peak,
+                       "note": "gathers of the candidates' 21 x 21 windows; near-duplicate candidates "
+                               "share windows, so most hit L2 (latency-bound, not HBM-bound)"}}
 
 
 def noise_rate(device, stream, imgs):
