@@ -53,9 +53,9 @@ FP64_PIPE_PEAK_GIPS = 152 * 2 * 2.07
 # predates the block test).
 FP64_MIX = {("mba", "chosen"): (0.119, 0.059, 0.012),
             ("batched", "chosen"): (2.692, 1.458, 0.314),
-            ("mba", "chosen_fp64_state"): (24.21, 13.56, 1.99),
-            ("mba", "plain"): (23.27, 12.05, 1.99),
-            ("mba", "plain_fp64"): (68.27, 43.06, 8.00),
+            ("mba", "chosen_fp64_state"): (23.71, 13.38, 1.98),
+            ("mba", "plain"): (22.95, 11.94, 1.98),
+            ("mba", "plain_fp64"): (67.95, 42.96, 7.98),
             ("batched", "chosen_fp64_state"): (32.06, 18.23, 2.04)}
 # The double-float state forms spend few FP64 instructions per sample and
 # are bound by instruction issue: one warp instruction per clock per
@@ -74,9 +74,9 @@ ISSUE_PER_SAMPLE = {("mba", "chosen"): 33.54, ("batched", "chosen"): 43.83}
 # grows more slowly than the orbit count: it is not scaled to the full
 # launch, whose own traffic stays null.
 TRAFFIC_SMALL_CASE = {("mba", "chosen"): (165297664, 343890136),
-                      ("mba", "chosen_fp64_state"): (142069504, 343890136),
-                      ("mba", "plain"): (177362176, 687780272),
-                      ("mba", "plain_fp64"): (177615104, 687780272)}
+                      ("mba", "chosen_fp64_state"): (142358272, 343890136),
+                      ("mba", "plain"): (178343680, 687780272),
+                      ("mba", "plain_fp64"): (177772544, 687780272)}
 
 
 def parse():
