@@ -864,12 +864,56 @@ def sparse_subrecord(args, rank, device, barrier, world, max_over_ranks, vet_par
         r, _ = bench_form(b, f, sky, stream, imgs, states, device, barrier,
                           vet_params if f.name == "chosen" else None)
         out[f.name] = form_record(r)
+    out["shuffled_orbits"] = footprint_record(b, sky, imgs, states, device)
     r = out["chosen"]
     out["value"] = r["samples_per_s"] * world
     out["unit"] = UNIT
     del imgs, states
     torch.cuda.empty_cache()
     return out
+
+
+def footprint_record(b, sky, imgs, states, device, steps=3):
+    """The sparse survey's orbits in a random order (families interleaved,
+    no family arrays), chosen form, with and without the footprint order
+    (ndt_set_footprint_sort): the stack_orbits call's time with CUDA events
+    on the context's stream (the ordering kernels included), the stack
+    kernel's own time and what the off-chip and block tests skipped."""
+    import torch
+    from paper_2503_08854_gb300 import ndt
+    n = states.shape[1]
+    gen = torch.Generator()
+    gen.manual_seed(17)
+    shuffled = states[:, torch.randperm(n, generator=gen).to(states.device)].contiguous()
+    stream = torch.cuda.Stream(device=device)
+    ctx = ndt.create(device.index, stream)
+    res = {"orbits": n, "order": "seeded random permutation of the survey's family-grouped orbits"}
+    try:
+        ndt.load_exposures(ctx, sky.ex, imgs, plane_dtype=b.plane)
+        ot, et = (int(x) for x in b.tiles.split(","))
+        ndt.set_launch(ctx, ndt.LAUNCH_PERSISTENT, ot, et, use_graph=True)
+        for name, on in (("unordered", False), ("footprint_ordered", True)):
+            ndt.set_footprint_sort(ctx, on)
+            for _ in range(2):
+                ndt.stack_orbits(ctx, shuffled, sky.t0, n)               # warm-up
+            ms = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ndt.stack_orbits(ctx, shuffled, sky.t0, n)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            st = ndt.get_stats(ctx)
+            t = statistics.mean(ms)
+            res[name] = {"call_ms": t, "stack_kernel_ms": st["last_stack_ms"],
+                         "stack_pairs_per_s": st["samples"] / (t / 1e3),
+                         "offchip_skipped_fraction": st["offchip_skipped"] / max(st["samples"], 1),
+                         "block_skipped_fraction": st["block_skipped"] / max(st["samples"], 1)}
+    finally:
+        ndt.destroy(ctx)
+    return res
 
 
 def main():

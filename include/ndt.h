@@ -276,6 +276,20 @@ ndt_status ndt_set_fp64_geometry(ndt_ctx *ctx, int32_t enabled);
    ignored. */
 ndt_status ndt_set_df_state(ndt_ctx *ctx, int32_t enabled);
 
+/* Footprint order (off by default): stack_orbits without families first
+   orders the orbits by their sky position at the middle exposure (Morton
+   interleave of the ecliptic longitude and latitude of their light-time
+   corrected direction, 16 bits each, from the stack's own propagation), so
+   that the orbits of a warp gather from the same image tiles and the
+   off-chip and block tests can skip whole warps (the paper batches orbits
+   for its GPU intersections, sec. 4.2.1; an unordered list defeats both
+   tests).  Results are those of the unordered walk (each orbit's sums do
+   not depend on its neighbours) and stay in the caller's order.  Costs one
+   propagation per orbit and a 4-pass radix sort of n 8-byte items per call,
+   with 16 n bytes of device scratch in the context.  Families given to
+   stack_orbits already group orbits and are used as given. */
+ndt_status ndt_set_footprint_sort(ndt_ctx *ctx, int32_t enabled);
+
 /*
  * autotune: time the persistent stack for every orbit_tile in {32, 64, 128}
  * and exp_tile in {8, 16, 32} on the given workload (arguments as for

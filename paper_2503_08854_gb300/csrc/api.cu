@@ -90,6 +90,8 @@ struct ndt_ctx {
   int32_t block_test = 1;  // warp cone test per exposure block (persistent form)
   int32_t geometry_fp64 = 0;  // plain form: FP64 light time and TAN projection
   int32_t state_df = 1;    // two-body state in double-float (both forms and predict_positions)
+  int32_t footprint = 0;   // stack_orbits without families: walk orbits in sky-footprint order
+  DevBuf fp_items, fp_hist;
   float broaden = 0.0f;    // filter broadening (px) for coarse searches
   double t_ref = 0.0;      // earliest exposure epoch (origin of ExpDev::tf)
   cudaGraphExec_t graph = nullptr;
@@ -366,7 +368,7 @@ void ndt_destroy(ndt_ctx* c) {
                     &c->cnn_labels, &c->cnn_out, &c->cnn_scratch, &c->cnn_params, &c->cnn_grad,
                     &c->dedup_scratch, &c->dedup_ref, &c->dedup_out, &c->count_dev,
                     &c->trim_bits, &c->trim_nu, &c->trim_n, &c->mad_imgs, &c->mad_state,
-                    &c->mad_hist, &c->mad_stage, &c->mad_cnt, &c->mad_buf};
+                    &c->mad_hist, &c->mad_stage, &c->mad_cnt, &c->mad_buf, &c->fp_items, &c->fp_hist};
   for (DevBuf* b : bufs) b->release();
   delete c;   // (the DevBuf destructors free anything not listed above)
 }
@@ -840,6 +842,21 @@ ndt_status ndt_stack_orbits(ndt_ctx* ctx, const double* states, double t0, int64
   a.block_test = persistent && ctx->offchip ? ctx->block_test : 0;
   a.geometry_fp64 = persistent ? 0 : ctx->geometry_fp64;
   a.state_df = ctx->state_df;
+  if (ctx->footprint && n_fam == 0 && n_orbits > 1) {
+    // orbits ordered by their sky direction at the middle exposure, so that
+    // a warp's orbits gather from the same image tiles and the off-chip and
+    // block tests can skip whole warps; outputs stay in the caller's order
+    NDT_CK(ctx->fp_items.ensure(16 * (size_t)n_orbits), "footprint keys");
+    NDT_CK(ctx->fp_hist.ensure(sort_hist_bytes(n_orbits)), "footprint histogram");
+    unsigned long long* ia = ctx->fp_items.as<unsigned long long>();
+    unsigned long long* sorted = nullptr;
+    NDT_CK(launch_footprint_order(a.states, n_orbits, t0, ctx->t_ref, a.ex, ctx->n_exp / 2, ctx->ph,
+                                  ctx->state_df != 0, ia, ia + n_orbits, ctx->fp_hist.as<unsigned int>(), &sorted,
+                                  ctx->stream),
+           "footprint order");
+    ctx->launches += 13;
+    a.order = sorted;
+  }
   s = run_stack(ctx, a);
   if (s != NDT_OK) return s;
   ctx->last_n = n_orbits;
@@ -994,6 +1011,12 @@ ndt_status ndt_set_fp64_geometry(ndt_ctx* ctx, int32_t enabled) {
 ndt_status ndt_set_df_state(ndt_ctx* ctx, int32_t enabled) {
   if (!ctx) return NDT_EINVAL;
   ctx->state_df = enabled ? 1 : 0;
+  return NDT_OK;
+}
+
+ndt_status ndt_set_footprint_sort(ndt_ctx* ctx, int32_t enabled) {
+  if (!ctx) return NDT_EINVAL;
+  ctx->footprint = enabled ? 1 : 0;
   return NDT_OK;
 }
 

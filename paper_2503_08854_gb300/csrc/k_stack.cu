@@ -308,8 +308,9 @@ template <int PT, int GEOM>
 __global__ void __launch_bounds__(kBlock, GEOM == 2 ? NDT_STACK_MINB_DF : NDT_STACK_MINB)
     k_stack_plain(const StackArgs a) {
   using W = typename std::conditional<GEOM == 2, WalkDF, Walk>::type;
-  const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-  const bool active = o < a.n;
+  const int64_t slot = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  const bool active = slot < a.n;
+  const int64_t o = active && a.order ? (int64_t)(uint32_t)__ldg(a.order + slot) : slot;
   W w;
   if (active) {
     walk_init(w, a.ph, a.states, a.n, o, a.t0, a.t_ref);
@@ -368,8 +369,9 @@ __global__ void __launch_bounds__(kBlock, DFS ? NDT_STACK_MINB_DF : NDT_STACK_MI
     const int f = __ldg(a.fam_order + fq);
     const int64_t tile = item - __ldg(a.item_off + fq);
     const int64_t o_begin = __ldg(a.fam_orb_off + f), o_end = __ldg(a.fam_orb_off + f + 1);
-    const int64_t o = o_begin + tile * TEAM + tl;
-    const bool active = o < o_end;
+    const int64_t slot = o_begin + tile * TEAM + tl;
+    const bool active = slot < o_end;
+    const int64_t o = active && a.order ? (int64_t)(uint32_t)__ldg(a.order + slot) : slot;
     const int64_t e_begin = __ldg(a.fam_exp_off + f), e_end = __ldg(a.fam_exp_off + f + 1);
     W w;
     if (active) {
@@ -421,6 +423,41 @@ __global__ void __launch_bounds__(kBlock, DFS ? NDT_STACK_MINB_DF : NDT_STACK_MI
     walk_finish(w, a, o, active);
     team_sync<TEAM>(team);   // every thread has read item_sh before it is rewritten
   }
+}
+
+// Bits of x (16 of them) spread to the even positions of a 32-bit word.
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
+  x &= 0x0000FFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+// Sky-footprint key of each orbit: the Morton interleave of the ecliptic
+// longitude and latitude (16 bits each) of its topocentric direction at
+// exposure j, from the stack's own step and light time (Track);
+// items[o] = key << 32 | o.  An orbit whose step fails sorts last.
+template <bool DFS>
+__global__ void __launch_bounds__(kBlock)
+    k_footprint_key(const double* __restrict__ states, int64_t n, double t0, double t_ref,
+                    const ExpDev* __restrict__ ex, int32_t j, Phys ph, unsigned long long* __restrict__ items) {
+  const int64_t o = (int64_t)blockIdx.x * kBlock + threadIdx.x;
+  if (o >= n) return;
+  Track<DFS> w;
+  w.init(ph, states, n, o, t0, t_ref);
+  uint32_t key = 0xFFFFFFFFu;
+  dfloat rho[3];
+  if (w.step(ph, ex[j], rho)) {
+    constexpr float kPiF = 3.14159265f;
+    const float x = rho[0].h, y = rho[1].h, z = rho[2].h;
+    const float lon = atan2f(y, x), lat = atan2f(z, sqrtf(x * x + y * y));
+    const float uf = fminf(fmaxf((lon + kPiF) * (65535.0f / (2.0f * kPiF)), 0.0f), 65535.0f);
+    const float vf = fminf(fmaxf((lat + 0.5f * kPiF) * (65535.0f / kPiF), 0.0f), 65535.0f);
+    key = spread_bits16((uint32_t)uf) | (spread_bits16((uint32_t)vf) << 1);
+  }
+  items[o] = ((unsigned long long)key << 32) | (unsigned long long)(uint32_t)o;
 }
 
 // One step of a walk to exposure e and its topocentric vector; false when
@@ -507,6 +544,21 @@ cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st) {
   else if (a.geometry_fp64) launch_plain_geom<1>(a, (unsigned)blocks, st);
   else launch_plain_geom<0>(a, (unsigned)blocks, st);
   return cudaGetLastError();
+}
+
+cudaError_t launch_footprint_order(const double* states, int64_t n, double t0, double t_ref, const ExpDev* ex,
+                                   int32_t j, Phys ph, bool state_df, unsigned long long* a,
+                                   unsigned long long* b, unsigned int* hist, unsigned long long** sorted,
+                                   cudaStream_t st) {
+  const int64_t blocks = (n + kBlock - 1) / kBlock;
+  if (blocks == 0) return cudaSuccess;
+  if (state_df)
+    k_footprint_key<true><<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, t_ref, ex, j, ph, a);
+  else
+    k_footprint_key<false><<<(unsigned)blocks, kBlock, 0, st>>>(states, n, t0, t_ref, ex, j, ph, a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sort_items_hi32(a, b, hist, n, 4, sorted, st);   // the 32-bit key: four 8-bit passes
 }
 
 cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st) {

@@ -1084,9 +1084,19 @@ struct StackArgs {
   int32_t block_test;          // persistent form: warp cone test per staged exposure block
   int32_t geometry_fp64;       // plain form: FP64 light time and TAN projection
   int32_t state_df;            // two-body state in double-float (WalkDF) instead of FP64
+  // footprint order (no families): slot o of the walk takes orbit
+  // (uint32) order[o]; null: slot o is orbit o
+  const unsigned long long* order;
 };
 
 cudaError_t launch_stack_plain(const StackArgs& a, cudaStream_t st);
+// Footprint order of n orbits (n < 2^32): keys of their sky direction at
+// exposure j (Morton interleave of ecliptic longitude and latitude, 16 bits
+// each) sorted with their indices; *sorted points into a or b, each n items.
+cudaError_t launch_footprint_order(const double* states, int64_t n, double t0, double t_ref, const ExpDev* ex,
+                                   int32_t j, Phys ph, bool state_df, unsigned long long* a,
+                                   unsigned long long* b, unsigned int* hist, unsigned long long** sorted,
+                                   cudaStream_t st);
 cudaError_t launch_stack_persistent(const StackArgs& a, int n_sms, cudaStream_t st);
 cudaError_t launch_predict(const double* states, int64_t n, double t0, double t_ref, const ExpDev* ex,
                            const int32_t* exp_pos_to_table, int32_t n_exp, Phys ph, bool state_df,

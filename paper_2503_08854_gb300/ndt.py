@@ -84,6 +84,7 @@ _lib.ndt_dedup_candidates.argtypes = [_vp, _vp, _f64, _i64, _vp, _i64, C.c_float
 _lib.ndt_set_block_test.argtypes = [_vp, _i32]
 _lib.ndt_set_fp64_geometry.argtypes = [_vp, _i32]
 _lib.ndt_set_df_state.argtypes = [_vp, _i32]
+_lib.ndt_set_footprint_sort.argtypes = [_vp, _i32]
 _lib.ndt_count_candidates.argtypes = [_vp, C.c_float, C.POINTER(_i64)]
 _lib.ndt_measure_fp64_rate.argtypes = [C.c_int, _i32, C.POINTER(_f64), C.POINTER(_f64)]
 
@@ -320,6 +321,12 @@ def set_df_state(ctx, enabled=True):
     _check(ctx, _lib.ndt_set_df_state(ctx, 1 if enabled else 0))
 
 
+def set_footprint_sort(ctx, enabled=True):
+    """ndt_set_footprint_sort: stack_orbits without families walks the orbits
+    in sky-footprint order (results in the caller's order)."""
+    _check(ctx, _lib.ndt_set_footprint_sort(ctx, 1 if enabled else 0))
+
+
 def set_block_test(ctx, enabled=True):
     """ndt_set_block_test: the persistent form's per-warp cone test of each
     staged exposure block."""
@@ -369,4 +376,4 @@ def exported_symbols():
             "ndt_cnn_forward", "ndt_cnn_loss_grad", "ndt_cnn_adam_step", "ndt_vet",
             "ndt_trim_candidates", "ndt_noise_mad", "ndt_selftest_wait_timeout", "ndt_topk_noalloc",
             "ndt_measure_fp64_rate", "ndt_dedup_candidates", "ndt_count_candidates",
-            "ndt_set_block_test", "ndt_set_fp64_geometry", "ndt_set_df_state"]
+            "ndt_set_block_test", "ndt_set_fp64_geometry", "ndt_set_df_state", "ndt_set_footprint_sort"]

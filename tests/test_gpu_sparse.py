@@ -83,3 +83,26 @@ def test_sparse_full_size_forms_count_the_same_samples(gpu, capsys):
               f"stack ms plain {st_plain['last_stack_ms']:.1f}, off-chip test "
               f"{st_off['last_stack_ms']:.1f}, + block test {st_on['last_stack_ms']:.1f}; block test "
               f"skipped {st_on['block_skipped'] / st_on['samples']:.4f} of the pairs")
+
+
+def test_footprint_order_matches_oracle_and_restores_skipping(gpu):
+    """The reduced survey's orbits in a random order (families interleaved):
+    with the footprint order (ndt_set_footprint_sort) both forms match the
+    oracle orbit by orbit, in the caller's order, and the persistent form's
+    block test skips at least as many samples as without it."""
+    sky = synth.sparse_sky(n_exp=3000, n_fam=8, fam_size=128, n_inj=4, seed=11)
+    imgs = _images(gpu, sky)
+    sky.states = sky.states[np.random.default_rng(5).permutation(len(sky.states))]
+    _stack(gpu, sky, imgs, "f32", "persistent")
+    st_shuffled = gpu.stats()
+    ndt.set_footprint_sort(gpu.ctx, True)
+    ordered = _stack(gpu, sky, imgs, "f32", "persistent")
+    st_ordered = gpu.stats()
+    plain = _stack(gpu, sky, imgs, "f32", "plain")
+    host = imgs.cpu().numpy()
+    ref = O.stack(sky.states, sky.t0, sky.ex, images=[host[j] for j in range(sky.ex.n)], nthreads=0)
+    check_stack({k: v.cpu().numpy() for k, v in ordered.items()}, ref)
+    check_stack({k: v.cpu().numpy() for k, v in plain.items()}, ref)
+    assert st_ordered["valid_samples"] == st_shuffled["valid_samples"]
+    assert st_ordered["block_skipped"] >= st_shuffled["block_skipped"], (st_ordered, st_shuffled)
+    assert st_ordered["block_skipped"] > 0.5 * st_ordered["samples"], st_ordered
